@@ -1,0 +1,224 @@
+/*
+ * svf.h -- C ABI of the B300 (sm_103a) streaming graph-ANNS hot path of
+ * SVFusion (arXiv 2601.08528): Build / Search / Insert / Delete over a
+ * vector store X_t and a fixed out-degree proximity graph G_t (Sec. 2.2,
+ * Sec. 2.3).
+ *
+ * Conventions
+ *  - Every call returns int: SVF_OK (0) or a negative SVF_E* code; the text
+ *    of the last error of the calling thread is svf_last_error().
+ *  - Pointers marked "device" are CUDA device pointers on the current
+ *    device; "host" pointers are ordinary CPU memory.  `stream` is a
+ *    cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Work is enqueued asynchronously on `stream`; outputs are valid once the
+ *    stream is synchronised.  Errors found on the device (a bad id in a
+ *    delete batch, an exhausted wait) are written to the index's status word
+ *    and returned by svf_sync() and by the next call on the index.
+ *  - Ownership: every device buffer is allocated by the caller (sizes from
+ *    svf_buffer_sizes) and BORROWED by the index, which allocates no device
+ *    memory.  The index itself is a small host object freed by svf_destroy.
+ *  - A call that fails validation changes nothing.
+ *  - Ids are 0-based uint32, assigned densely in insertion order and never
+ *    reused (the paper numbers host ids from 1, Sec. 4.2); ids must stay
+ *    below 2^30.  SVF_EMPTY marks an unused graph slot / missing result.
+ *  - Distances: squared L2, or the negated inner product -<q,x> (so smaller
+ *    is nearer in both).  Every order is lexicographic (distance, id).
+ */
+#ifndef SVF_H
+#define SVF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SVF_OK 0
+#define SVF_EINVAL (-1)    /* bad argument (sizes, ids, null pointers) */
+#define SVF_ECAPACITY (-2) /* n_used + m would exceed n_cap */
+#define SVF_ECUDA (-3)     /* a CUDA runtime call failed */
+#define SVF_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define SVF_EBOUNDS (-5)   /* a device-side range check failed */
+#define SVF_EDEVICE (-6)   /* other device-side error */
+
+#define SVF_EMPTY 0xFFFFFFFFu
+
+enum svf_dtype { SVF_F32 = 0, SVF_U8 = 1, SVF_BF16 = 2, SVF_FP8 = 3 };
+enum svf_metric { SVF_L2 = 0, SVF_IP = 1 };
+enum svf_prune_mode { SVF_PRUNE_RNG = 0, SVF_PRUNE_RANK = 1 };
+
+/* Index parameters.
+ *   d        dimension, a multiple of 16, 16..2048
+ *   dtype    primary store: SVF_F32 or SVF_U8 (u8 distances are exact int32)
+ *   metric   SVF_L2 or SVF_IP
+ *   R        out-degree: 32 or 64 (Sec. 2.3: fixed out-degree KNNG)
+ *   n_cap    capacity in vectors (< 2^30)
+ *   prune    neighbour reordering rule (Sec. 5.1): SVF_PRUNE_RNG counts
+ *            candidates j < i with dist(c_j, c_i) < dist(v, c_i);
+ *            SVF_PRUNE_RANK counts j < i whose list contains c_i
+ *   repair_c entries taken from each deleted neighbour's list in the
+ *            localized repair (Sec. 5.2; the paper uses c = 8)
+ *   lowp     bit 0: keep a bfloat16 copy, bit 1: keep an FP8-E4M3 copy with
+ *            a per-vector fp32 scale (F32 primary only)
+ *   seed     default seed of the random pool initialisation (Alg. 1) */
+typedef struct {
+    int32_t d;
+    int32_t dtype;
+    int32_t metric;
+    int32_t R;
+    int64_t n_cap;
+    int32_t prune;
+    int32_t repair_c;
+    int32_t lowp;
+    int32_t reserved0;
+    uint64_t seed;
+} svf_params;
+
+/* Byte sizes of the caller-allocated device buffers (all 256-byte aligned). */
+typedef struct {
+    size_t vecs;      /* n_cap rows of d*esize bytes (primary store) */
+    size_t vecs_bf16; /* n_cap rows of 2d bytes, 0 unless lowp bit 0 */
+    size_t vecs_fp8;  /* n_cap rows of fp8_pitch = roundup(d + 4, 32) bytes: codes, then the fp32 scale */
+    size_t graph;     /* n_cap * R uint32 */
+    size_t del_bits;  /* ceil(n_cap / 32) uint32 */
+    size_t workspace; /* scratch for build / insert / delete of up to max_batch vectors */
+    size_t status;    /* status word and counters */
+} svf_sizes;
+
+/* Device buffers, borrowed by the index for its lifetime.  vecs, graph,
+ * del_bits, workspace and status are required; the low-precision stores
+ * are required iff the matching lowp bit is set.  svf_create zeroes
+ * del_bits and status and sets every graph slot to SVF_EMPTY. */
+typedef struct {
+    void *vecs;
+    void *vecs_bf16;
+    void *vecs_fp8;
+    uint32_t *graph;
+    uint32_t *del_bits;
+    void *workspace;
+    size_t ws_bytes;
+    void *status;
+    size_t status_bytes;
+} svf_buffers;
+
+/* Search parameters (Alg. 1 with a fixed iteration count).
+ *   k         results per query, 1 <= k <= min(L, 32)
+ *   L         candidate pool size (itopk): 32, 64, 128 or 256
+ *   T         iterations; one parent (the nearest unexpanded pool entry) is
+ *             expanded per iteration; an iteration with none left is a no-op
+ *   precision traversal store: SVF_F32/SVF_U8 (primary), SVF_BF16, SVF_FP8
+ *   rerank    1: recompute the final pool's distances exactly from the
+ *             primary store and re-sort before taking k (low precision only)
+ *   mlp       device pointer to a packed stop network (svf_mlp_pack layout)
+ *             or NULL; with it the query stops after iteration t once
+ *             t+1 >= t_min and z >= z_tau (z = the network's logit)
+ *   qkeys     device, nq uint64 query keys, or NULL: key = wrapping sum over
+ *             the query's 32-bit words w_i of splitmix64((i << 32) | w_i)
+ *   seed      pool-initialisation seed (0: the index's seed)
+ *   hash_log2 per-query visited-table size, log2 of slots (0: automatic)
+ *   trace_feat  device [nq][T][16] float, or NULL: per-iteration features
+ *   trace_meta  device [nq][2] int32 (iterations run, last top-k change)
+ *   pool_out  device [nq][L] uint64 keys of the final pool, or NULL */
+typedef struct {
+    int32_t k;
+    int32_t L;
+    int32_t T;
+    int32_t precision;
+    int32_t rerank;
+    int32_t t_min;
+    const void *mlp;
+    float z_tau;
+    int32_t hash_log2;
+    const uint64_t *qkeys;
+    uint64_t seed;
+    float *trace_feat;
+    int32_t *trace_meta;
+    uint64_t *pool_out;
+} svf_search_params;
+
+/* Running counters (since svf_create or svf_stats_reset). */
+typedef struct {
+    int64_t n_used;
+    int64_t n_deleted;
+    uint64_t search_queries;
+    uint64_t search_iters;      /* parents expanded */
+    uint64_t search_evals;      /* distance evaluations in traversal */
+    uint64_t hash_resets;       /* visited-table resets */
+    uint64_t repaired_rows;     /* rows rewritten by localized repair */
+    uint64_t reverse_targets;   /* rows whose tail took reverse edges */
+} svf_counters;
+
+typedef struct svf_index svf_index;
+
+const char *svf_last_error(void);
+
+/* Buffer sizes for an index of `p` that builds / inserts / deletes at most
+ * max_batch vectors per call (build needs max_batch >= n). */
+int svf_buffer_sizes(const svf_params *p, int64_t max_batch, svf_sizes *out);
+
+/* Create an index over caller-allocated device buffers (host handle out). */
+int svf_create(const svf_params *p, const svf_buffers *b, svf_index **out);
+int svf_destroy(svf_index *h);
+
+/* Declare that the buffers already hold n_used valid rows, graph rows and
+ * deletion bits (an index restored from a file or built elsewhere). */
+int svf_attach(svf_index *h, int64_t n_used);
+
+/* Build (Sec. 2.2 Build, Sec. 4.2 Index Construction): X is device, n rows
+ * of d primary elements (n <= n_cap, n <= max_batch).  Copies X into the
+ * store, computes the exact 2R nearest neighbours of every row (self
+ * excluded) and prunes each list to R (Sec. 5.1 reordering).  Resets
+ * deletions; n_used = n. */
+int svf_build(svf_index *h, const void *X, int64_t n, void *stream);
+
+/* Search (Alg. 1): Q is device, nq rows of d elements (uint8 for a U8
+ * index, fp32 otherwise).  out_ids: device [nq][k] uint32; out_dist:
+ * device [nq][k], int32 for a U8 index and float otherwise.  Missing
+ * results are SVF_EMPTY / +inf (INT32_MAX for U8). */
+int svf_search(svf_index *h, const void *Q, int64_t nq, const svf_search_params *sp, uint32_t *out_ids,
+               void *out_dist, void *stream);
+
+/* Insert (Sec. 5.1): X is device, m rows.  The new ids are n_used ..
+ * n_used+m-1 (written to out_ids, device, if not NULL).  Each new vector
+ * searches the pre-call graph (pool L_ins, T_ins iterations), its pool is
+ * reordered into its row, and every chosen neighbour u keeps the R/2 best
+ * (distance, id) of its tail half [R/2, R) and the new vertices that chose
+ * it.  L_ins: 32..256 power of two >= R. */
+int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_ins, uint32_t *out_ids,
+               void *stream);
+
+/* Delete (Sec. 5.2): ids is device, m uint32.  Any id >= n_used fails the
+ * whole call (SVF_EINVAL reported by svf_sync; nothing changes); ids already
+ * deleted are counted no-ops.  Sets the bits, then repairs every live vertex
+ * with more than R/2 deleted neighbours from a snapshot of the graph.
+ * out_newly (device int64, optional) receives the number newly deleted. */
+int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly, void *stream);
+
+/* Wait for the index's last stream and report any device-side error. */
+int svf_sync(svf_index *h);
+
+/* Counters (synchronises). */
+int svf_stats(svf_index *h, svf_counters *out);
+int svf_stats_reset(svf_index *h);
+
+/* Encode fp32 rows into the low-precision layouts (device to device):
+ * bf16 = round-to-nearest-even; FP8 row = E4M3(x_i / s) with satfinite and
+ * s = max|x| / 448 (1 if 0) stored as fp32 at byte d. */
+int svf_encode_bf16(const float *X, int64_t n, int32_t d, void *out, void *stream);
+int svf_encode_fp8(const float *X, int64_t n, int32_t d, void *out, int64_t pitch, void *stream);
+
+/* Exact brute-force k nearest neighbours (ground truth, Sec. 6.1 "exhaustive
+ * linear scan"): for each of nq device queries the k <= 128 rows of the
+ * device store X (n rows of d elements, dtype F32 or U8, metric as in an
+ * index) with the smallest (distance, id), skipping row self[i] if self
+ * (device int64 [nq]) is given.  work_keys: device scratch [nq][k] uint64
+ * (caller-allocated).  out_ids device [nq][k] uint32, out_dist device
+ * [nq][k] (int32 for U8, float otherwise; may be NULL). */
+int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, const void *Q, int64_t nq,
+            const int64_t *self, int32_t k, uint64_t *work_keys, uint32_t *out_ids, void *out_dist, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVF_H */

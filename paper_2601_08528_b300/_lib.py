@@ -1,0 +1,102 @@
+"""ctypes binding of libsvf.so (include/svf.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+passes pointers and sizes.  There is no fallback: if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsvf.so")
+
+SVF_OK, SVF_EINVAL, SVF_ECAPACITY, SVF_ECUDA, SVF_ETIMEOUT, SVF_EBOUNDS, SVF_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+EMPTY = 0xFFFFFFFF
+F32, U8, BF16, FP8 = 0, 1, 2, 3
+L2, IP = 0, 1
+PRUNE_RNG, PRUNE_RANK = 0, 1
+
+# every symbol include/svf.h declares
+SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "svf_attach", "svf_build", "svf_search",
+           "svf_insert", "svf_delete", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
+           "svf_encode_fp8", "svf_knn"]
+
+
+class Params(C.Structure):
+    _fields_ = [("d", C.c_int32), ("dtype", C.c_int32), ("metric", C.c_int32), ("R", C.c_int32),
+                ("n_cap", C.c_int64), ("prune", C.c_int32), ("repair_c", C.c_int32), ("lowp", C.c_int32),
+                ("reserved0", C.c_int32), ("seed", C.c_uint64)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("vecs", C.c_size_t), ("vecs_bf16", C.c_size_t), ("vecs_fp8", C.c_size_t), ("graph", C.c_size_t),
+                ("del_bits", C.c_size_t), ("workspace", C.c_size_t), ("status", C.c_size_t)]
+
+
+class Buffers(C.Structure):
+    _fields_ = [("vecs", C.c_void_p), ("vecs_bf16", C.c_void_p), ("vecs_fp8", C.c_void_p), ("graph", C.c_void_p),
+                ("del_bits", C.c_void_p), ("workspace", C.c_void_p), ("ws_bytes", C.c_size_t),
+                ("status", C.c_void_p), ("status_bytes", C.c_size_t)]
+
+
+class SearchParams(C.Structure):
+    _fields_ = [("k", C.c_int32), ("L", C.c_int32), ("T", C.c_int32), ("precision", C.c_int32),
+                ("rerank", C.c_int32), ("t_min", C.c_int32), ("mlp", C.c_void_p), ("z_tau", C.c_float),
+                ("hash_log2", C.c_int32), ("qkeys", C.c_void_p), ("seed", C.c_uint64), ("trace_feat", C.c_void_p),
+                ("trace_meta", C.c_void_p), ("pool_out", C.c_void_p)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("n_used", C.c_int64), ("n_deleted", C.c_int64), ("search_queries", C.c_uint64),
+                ("search_iters", C.c_uint64), ("search_evals", C.c_uint64), ("hash_resets", C.c_uint64),
+                ("repaired_rows", C.c_uint64), ("reverse_targets", C.c_uint64)]
+
+
+class SvfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"svf error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libsvf.so from the package directory (no other location)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2601_08528_b300/build.py (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "svf_last_error": (C.c_char_p, []),
+        "svf_buffer_sizes": (I32, [C.POINTER(Params), I64, C.POINTER(Sizes)]),
+        "svf_create": (I32, [C.POINTER(Params), C.POINTER(Buffers), C.POINTER(C.c_void_p)]),
+        "svf_destroy": (I32, [P]),
+        "svf_attach": (I32, [P, I64]),
+        "svf_build": (I32, [P, P, I64, P]),
+        "svf_search": (I32, [P, P, I64, C.POINTER(SearchParams), P, P, P]),
+        "svf_insert": (I32, [P, P, I64, I32, I32, P, P]),
+        "svf_delete": (I32, [P, P, I64, P, P]),
+        "svf_sync": (I32, [P]),
+        "svf_stats": (I32, [P, C.POINTER(Counters)]),
+        "svf_stats_reset": (I32, [P]),
+        "svf_encode_bf16": (I32, [P, I64, I32, P, P]),
+        "svf_encode_fp8": (I32, [P, I64, I32, P, I64, P]),
+        "svf_knn": (I32, [P, I64, I32, I32, I32, P, I64, P, I32, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(rc: int) -> None:
+    if rc != SVF_OK:
+        raise SvfError(rc, load().svf_last_error().decode())

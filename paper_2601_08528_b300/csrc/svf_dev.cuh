@@ -1,0 +1,393 @@
+// svf_dev.cuh -- device building blocks of the SVFusion graph-ANNS hot path
+// for B300 (sm_103a): (distance, id) keys, the counter-based generator of the
+// random pool initialisation (Alg. 1), warp-wide bitonic sort/merge of keys,
+// and team-of-8-lanes distance evaluation over 16-byte row chunks.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "../../include/svf.h"
+
+namespace svf {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kIdMask = 0x3FFFFFFFu;          // ids < 2^30
+constexpr uint32_t kExpBit = 0x80000000u;          // pool entry already expanded
+constexpr uint32_t kNewBit = 0x40000000u;          // admitted in this iteration
+constexpr uint64_t kCmpMask = 0xFFFFFFFF3FFFFFFFull;  // order ignores both flags
+constexpr uint64_t kPad = 0xFFFFFFFFFFFFFFFFull;   // +inf, flags set, id EMPTY
+constexpr int kTeam = 8;                           // lanes per distance
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------- keys
+// A 64-bit key is (distance key << 32) | id, compared with the flag bits
+// masked, so keys order lexicographically by (distance, id).
+__device__ __forceinline__ uint64_t cmpk(uint64_t k) { return k & kCmpMask; }
+
+// Order-preserving map of a float to uint32 (-0 folded into +0).
+__device__ __forceinline__ uint32_t fkey(float f) {
+    if (f == 0.0f) f = 0.0f;
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+__device__ __forceinline__ uint64_t make_key(uint32_t dk, uint32_t id) {
+    return ((uint64_t)dk << 32) | id;
+}
+__device__ __forceinline__ uint32_t key_id(uint64_t k) { return (uint32_t)k & kIdMask; }
+__device__ __forceinline__ bool key_is_pad(uint64_t k) { return (uint32_t)(k >> 32) == 0xFFFFFFFFu; }
+
+// ---------------------------------------------------------------- generator
+// splitmix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): one counter-based mixing step.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool is_deleted(const uint32_t *__restrict__ del, uint32_t id) {
+    return (__ldg(del + (id >> 5)) >> (id & 31)) & 1u;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src), hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl64_xor(uint64_t v, int m) {
+    uint32_t lo = __shfl_xor_sync(kFull, (uint32_t)v, m), hi = __shfl_xor_sync(kFull, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ void cswap_keep(uint64_t &a, uint64_t other, bool keep_min) {
+    bool less = cmpk(other) < cmpk(a);
+    if (less == keep_min) a = other;
+}
+
+// ---------------------------------------------------------------- warp sorts
+// N = 32*S keys in a warp: element e = s*32 + lane lives in k[s] of `lane`.
+// Full bitonic sort, ascending.
+template <int S>
+__device__ __forceinline__ void warp_sort(uint64_t (&k)[S], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * S; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int ss = stride >> 5;
+#pragma unroll
+                for (int s = 0; s < S; s++) {
+                    if (s & ss) continue;
+                    const int e = s * 32 + lane;
+                    const bool asc = (e & size) == 0;
+                    uint64_t a = k[s], b = k[s | ss];
+                    bool sw = (cmpk(b) < cmpk(a)) == asc;
+                    k[s] = sw ? b : a;
+                    k[s | ss] = sw ? a : b;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; s++) {
+                    const int e = s * 32 + lane;
+                    const bool asc = (e & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    uint64_t o = shfl64_xor(k[s], stride);
+                    cswap_keep(k[s], o, lower == asc);
+                }
+            }
+        }
+    }
+}
+
+// Sort a bitonic sequence of 32*S keys ascending (half-cleaner cascade).
+template <int S>
+__device__ __forceinline__ void warp_bitonic_merge(uint64_t (&k)[S], int lane) {
+#pragma unroll
+    for (int stride = 16 * S; stride > 0; stride >>= 1) {
+        if (stride >= 32) {
+            const int ss = stride >> 5;
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                if (s & ss) continue;
+                uint64_t a = k[s], b = k[s | ss];
+                bool sw = cmpk(b) < cmpk(a);
+                k[s] = sw ? b : a;
+                k[s | ss] = sw ? a : b;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                uint64_t o = shfl64_xor(k[s], stride);
+                cswap_keep(k[s], o, (lane & stride) == 0);
+            }
+        }
+    }
+}
+
+// pool (32*LW, sorted) <- the 32*LW smallest of pool and cand (32*S, sorted).
+template <int LW, int S>
+__device__ __forceinline__ void warp_merge_into(uint64_t (&pool)[LW], const uint64_t (&cand)[S], int lane) {
+    static_assert(S <= LW, "candidate list longer than the pool");
+#pragma unroll
+    for (int s = LW - S; s < LW; s++) {
+        uint64_t r = shfl64(cand[LW - 1 - s], 31 - lane);
+        if (cmpk(r) < cmpk(pool[s])) pool[s] = r;
+    }
+    warp_bitonic_merge<LW>(pool, lane);
+}
+
+// ---------------------------------------------------------------- distances
+// A row is split into 16-byte chunks; the 8 lanes of a team take chunks
+// sub, sub+8, sub+16, ... and the partial sums are combined by xor shuffles
+// within the team, in a fixed order.  The query sits in shared memory as
+// fp32 (uint8 for a U8 index) in the same chunk layout as the row's values.
+struct RowDesc {
+    const uint8_t *base;  // store base
+    int64_t pitch;        // bytes per row
+    int nchunk;           // 16-byte chunks of values per row
+    int d;
+    int dtype;            // traversal dtype
+    int metric;
+};
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+}
+__device__ __forceinline__ float l2_4(float4 q, float4 x, float acc) {
+    float dx = q.x - x.x, dy = q.y - x.y, dz = q.z - x.z, dw = q.w - x.w;
+    acc = fmaf(dx, dx, acc);
+    acc = fmaf(dy, dy, acc);
+    acc = fmaf(dz, dz, acc);
+    return fmaf(dw, dw, acc);
+}
+__device__ __forceinline__ float4 bf2_to_f4(uint32_t a, uint32_t b) {
+    return make_float4(__uint_as_float(a << 16), __uint_as_float(a & 0xFFFF0000u), __uint_as_float(b << 16),
+                       __uint_as_float(b & 0xFFFF0000u));
+}
+__device__ __forceinline__ float4 fp8x4_to_f4(uint32_t w) {
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+    float2 a = __half22float2(*reinterpret_cast<__half2 *>(&lo));
+    float2 b = __half22float2(*reinterpret_cast<__half2 *>(&hi));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Partial (per-lane) accumulation of one 16-byte row chunk `c` against the
+// query.  qf: fp32 query in smem; qb: uint8 query in smem.  For FP8 the
+// values are codes; IP multiplies by the scale after the reduction, L2
+// applies it per element.
+template <int DT>
+__device__ __forceinline__ void chunk_acc(int metric, const uint4 v, int c, const float *qf, const uint8_t *qb,
+                                          float scale, float &facc, uint32_t &iacc) {
+    if constexpr (DT == SVF_F32) {
+        float4 x = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                               __uint_as_float(v.w));
+        float4 q = reinterpret_cast<const float4 *>(qf)[c];
+        facc = metric == SVF_L2 ? l2_4(q, x, facc) : dot4(q, x, facc);
+    } else if constexpr (DT == SVF_U8) {
+        uint4 q = reinterpret_cast<const uint4 *>(qb)[c];
+        if (metric == SVF_L2) {
+            uint32_t a = __vabsdiffu4(v.x, q.x), b = __vabsdiffu4(v.y, q.y), e = __vabsdiffu4(v.z, q.z),
+                     f = __vabsdiffu4(v.w, q.w);
+            iacc = __dp4a(a, a, iacc);
+            iacc = __dp4a(b, b, iacc);
+            iacc = __dp4a(e, e, iacc);
+            iacc = __dp4a(f, f, iacc);
+        } else {
+            iacc = __dp4a(v.x, q.x, iacc);
+            iacc = __dp4a(v.y, q.y, iacc);
+            iacc = __dp4a(v.z, q.z, iacc);
+            iacc = __dp4a(v.w, q.w, iacc);
+        }
+    } else if constexpr (DT == SVF_BF16) {
+        const float4 *q = reinterpret_cast<const float4 *>(qf) + 2 * c;
+        float4 x0 = bf2_to_f4(v.x, v.y), x1 = bf2_to_f4(v.z, v.w);
+        if (metric == SVF_L2) {
+            facc = l2_4(q[0], x0, facc);
+            facc = l2_4(q[1], x1, facc);
+        } else {
+            facc = dot4(q[0], x0, facc);
+            facc = dot4(q[1], x1, facc);
+        }
+    } else {  // FP8
+        const float4 *q = reinterpret_cast<const float4 *>(qf) + 4 * c;
+        float4 x[4] = {fp8x4_to_f4(v.x), fp8x4_to_f4(v.y), fp8x4_to_f4(v.z), fp8x4_to_f4(v.w)};
+        if (metric == SVF_L2) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                float4 xs = make_float4(x[u].x * scale, x[u].y * scale, x[u].z * scale, x[u].w * scale);
+                facc = l2_4(q[u], xs, facc);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++) facc = dot4(q[u], x[u], facc);
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t finish_key(int metric, float facc, uint32_t iacc, float scale) {
+    if constexpr (DT == SVF_U8) {
+        // L2: the exact non-negative int; IP: -dot through the order-
+        // preserving int32 -> uint32 map (sign bit flipped).
+        if (metric == SVF_L2) return iacc;
+        return (uint32_t)(-(int32_t)iacc) ^ 0x80000000u;
+    } else {
+        if (DT == SVF_FP8 && metric == SVF_IP) facc *= scale;
+        return fkey(metric == SVF_L2 ? facc : -facc);
+    }
+}
+
+// Distance keys of two rows for one team of 8 lanes (valid flags are
+// uniform within the team).  Every chunk load of both rows is issued before
+// any arithmetic so a team keeps up to 2 x 4 x 16 B per lane in flight.
+template <int DT>
+__device__ __forceinline__ void team_dist_key2(const RowDesc &R, uint32_t ida, bool va, uint32_t idb, bool vb,
+                                               int sub, const float *qf, const uint8_t *qb, uint32_t &ka,
+                                               uint32_t &kb) {
+    float fa = 0.0f, fb = 0.0f, sa = 1.0f, sb = 1.0f;
+    uint32_t ia = 0, ib = 0;
+    const uint8_t *ra = R.base + (int64_t)ida * R.pitch;
+    const uint8_t *rb = R.base + (int64_t)idb * R.pitch;
+    if (DT == SVF_FP8) {
+        if (va) sa = __ldg(reinterpret_cast<const float *>(ra + R.d));
+        if (vb) sb = __ldg(reinterpret_cast<const float *>(rb + R.d));
+    }
+    for (int c0 = sub; c0 < R.nchunk; c0 += 4 * kTeam) {
+        uint4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int c = c0 + u * kTeam;
+            if (va && c < R.nchunk) a[u] = __ldg(reinterpret_cast<const uint4 *>(ra) + c);
+            if (vb && c < R.nchunk) b[u] = __ldg(reinterpret_cast<const uint4 *>(rb) + c);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int c = c0 + u * kTeam;
+            if (va && c < R.nchunk) chunk_acc<DT>(R.metric, a[u], c, qf, qb, sa, fa, ia);
+            if (vb && c < R.nchunk) chunk_acc<DT>(R.metric, b[u], c, qf, qb, sb, fb, ib);
+        }
+    }
+#pragma unroll
+    for (int m = kTeam / 2; m > 0; m >>= 1) {
+        if constexpr (DT == SVF_U8) {
+            ia += __shfl_xor_sync(kFull, ia, m);
+            ib += __shfl_xor_sync(kFull, ib, m);
+        } else {
+            fa += __shfl_xor_sync(kFull, fa, m);
+            fb += __shfl_xor_sync(kFull, fb, m);
+        }
+    }
+    ka = finish_key<DT>(R.metric, fa, ia, sa);
+    kb = finish_key<DT>(R.metric, fb, ib, sb);
+}
+
+// Keys of list[0..n) written to keys[0..n) (id | flags): 8 rows per warp step.
+template <int DT>
+__device__ __forceinline__ void dist_list(const RowDesc &R, const uint32_t *list, int n, uint64_t *keys,
+                                          uint32_t flags, int lane, const float *qf, const uint8_t *qb) {
+    const int team = lane >> 3, sub = lane & 7;
+    for (int i0 = 0; i0 < n; i0 += 2 * (32 / kTeam)) {
+        int ia = i0 + team, ib = i0 + (32 / kTeam) + team;
+        bool va = ia < n, vb = ib < n;
+        uint32_t ida = va ? list[ia] : 0u, idb = vb ? list[ib] : 0u;
+        uint32_t ka, kb;
+        team_dist_key2<DT>(R, ida, va, idb, vb, sub, qf, qb, ka, kb);
+        if (sub == 0) {
+            if (va) keys[ia] = make_key(ka, ida | flags);
+            if (vb) keys[ib] = make_key(kb, idb | flags);
+        }
+    }
+}
+
+// Distance key between two rows of a primary store (F32 or U8), one team:
+// lane `sub` takes chunks sub, sub+8, ...; the same chunk order and
+// arithmetic as the query path, so dist(x_u, x_v) computed here equals the
+// search kernel's dist(q = x_v, x_u) bit for bit.
+template <int DT>
+__device__ __forceinline__ uint32_t team_pair_key(int metric, const uint4 *ra, const uint4 *rb, int nchunk, int sub) {
+    float f = 0.0f;
+    uint32_t ia = 0;
+    for (int c0 = sub; c0 < nchunk; c0 += 4 * kTeam) {
+        uint4 va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int c = c0 + u * kTeam;
+            if (c < nchunk) {
+                va[u] = ra[c];
+                vb[u] = rb[c];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int c = c0 + u * kTeam;
+            if (c >= nchunk) continue;
+            if constexpr (DT == SVF_U8) {
+                if (metric == SVF_L2) {
+                    uint32_t a = __vabsdiffu4(vb[u].x, va[u].x), b = __vabsdiffu4(vb[u].y, va[u].y),
+                             e = __vabsdiffu4(vb[u].z, va[u].z), g = __vabsdiffu4(vb[u].w, va[u].w);
+                    ia = __dp4a(a, a, ia);
+                    ia = __dp4a(b, b, ia);
+                    ia = __dp4a(e, e, ia);
+                    ia = __dp4a(g, g, ia);
+                } else {
+                    ia = __dp4a(vb[u].x, va[u].x, ia);
+                    ia = __dp4a(vb[u].y, va[u].y, ia);
+                    ia = __dp4a(vb[u].z, va[u].z, ia);
+                    ia = __dp4a(vb[u].w, va[u].w, ia);
+                }
+            } else {
+                float4 qa = make_float4(__uint_as_float(va[u].x), __uint_as_float(va[u].y), __uint_as_float(va[u].z),
+                                        __uint_as_float(va[u].w));
+                float4 xb = make_float4(__uint_as_float(vb[u].x), __uint_as_float(vb[u].y), __uint_as_float(vb[u].z),
+                                        __uint_as_float(vb[u].w));
+                f = metric == SVF_L2 ? l2_4(qa, xb, f) : dot4(qa, xb, f);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = kTeam / 2; m > 0; m >>= 1) {
+        if constexpr (DT == SVF_U8)
+            ia += __shfl_xor_sync(kFull, ia, m, kTeam);
+        else
+            f += __shfl_xor_sync(kFull, f, m, kTeam);
+    }
+    return finish_key<DT>(metric, f, ia, 1.0f);
+}
+
+// Output value of a distance key: float, or int32 for a U8 store.
+__device__ __forceinline__ uint32_t key_to_out(uint32_t dk, int dtype, int metric) {
+    if (dk == 0xFFFFFFFFu) return dtype == SVF_U8 ? 0x7FFFFFFFu : 0x7F800000u;  // INT32_MAX / +inf
+    if (dtype == SVF_U8) return metric == SVF_L2 ? dk : (dk ^ 0x80000000u);
+    return __float_as_uint(fkey_inv(dk));
+}
+
+// Status block layout (uint64 words).
+enum StatusWord {
+    kStError = 0,     // first device-side error code (int, 0 = none)
+    kStDetail = 1,    // detail of that error
+    kStQueries = 2,
+    kStIters = 3,
+    kStEvals = 4,
+    kStResets = 5,
+    kStRepaired = 6,
+    kStRevTargets = 7,
+    kStNewlyDeleted = 8,
+    kStScratch0 = 16,  // per-call scratch counters
+    kStWords = 64
+};
+
+__device__ __forceinline__ void set_error(unsigned long long *st, int code, long long detail) {
+    if (atomicCAS(st + kStError, 0ull, (unsigned long long)(unsigned)(-code)) == 0ull)
+        st[kStDetail] = (unsigned long long)detail;
+}
+
+}  // namespace svf

@@ -1,0 +1,197 @@
+"""A graph index on one GPU: torch allocates the device buffers, libsvf runs.
+
+``Index`` owns torch tensors for every buffer the C ABI borrows and forwards
+Build / Search / Insert / Delete (SVFusion Sec. 2.2) to the library.  Nothing
+here computes: inputs are checked for dtype/shape/device and passed by
+pointer on the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class SearchConfig:
+    k: int = 10
+    L: int = 64
+    T: int = 32
+    precision: str | None = None   # None: primary; "bf16" / "fp8"
+    rerank: bool = False
+    seed: int = 0
+    hash_log2: int = 0
+    mlp: torch.Tensor | None = None  # packed bf16 stop network (device)
+    tau: float = 0.5
+    t_min: int = 4
+
+
+class Index:
+    def __init__(self, d: int, n_cap: int, dtype: str = "f32", metric: str = "l2", R: int = 32,
+                 prune: str = "rng", repair_c: int = 8, lowp: tuple[str, ...] = (), seed: int = 0x5F0C,
+                 max_batch: int = 100_000, device: str | torch.device = "cuda"):
+        lib = L.load()
+        dev = torch.device(device)
+        if dev.type == "cuda" and dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.d, self.n_cap, self.R = d, n_cap, R
+        self.dtype, self.metric = dtype, metric
+        self.params = L.Params(d, L.U8 if dtype == "u8" else L.F32, L.IP if metric == "ip" else L.L2, R, n_cap,
+                               L.PRUNE_RANK if prune == "rank" else L.PRUNE_RNG, repair_c,
+                               (1 if "bf16" in lowp else 0) | (2 if "fp8" in lowp else 0), 0, seed)
+        sz = L.Sizes()
+        L.check(lib.svf_buffer_sizes(C.byref(self.params), max(1, max_batch), C.byref(sz)))
+        u8 = torch.uint8
+
+        def buf(nbytes):
+            return torch.empty(max(int(nbytes), 256), dtype=u8, device=self.device) if nbytes else None
+
+        self.vecs = buf(sz.vecs)
+        self.vecs_bf16 = buf(sz.vecs_bf16)
+        self.vecs_fp8 = buf(sz.vecs_fp8)
+        self.graph_buf = buf(sz.graph)
+        self.del_buf = buf(sz.del_bits)
+        self.workspace = buf(sz.workspace)
+        self.status = buf(sz.status)
+        b = L.Buffers(self.vecs.data_ptr(), _ptr(self.vecs_bf16) and self.vecs_bf16.data_ptr(),
+                      _ptr(self.vecs_fp8) and self.vecs_fp8.data_ptr(), self.graph_buf.data_ptr(),
+                      self.del_buf.data_ptr(), self.workspace.data_ptr(), self.workspace.numel(),
+                      self.status.data_ptr(), self.status.numel())
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(lib.svf_create(C.byref(self.params), C.byref(b), C.byref(h)))
+        self._h = h
+        self.n_used = 0
+
+    # ------------------------------------------------------------ views
+    @property
+    def graph(self) -> torch.Tensor:
+        """[n_cap, R] int32 view of the graph (0xFFFFFFFF reads as -1)."""
+        return self.graph_buf[: self.n_cap * self.R * 4].view(torch.int32).view(self.n_cap, self.R)
+
+    @property
+    def del_bits(self) -> torch.Tensor:
+        return self.del_buf[: (self.n_cap + 31) // 32 * 4].view(torch.int32)
+
+    def vectors(self) -> torch.Tensor:
+        esz = 1 if self.dtype == "u8" else 4
+        t = self.vecs[: self.n_cap * self.d * esz]
+        return t.view(self.n_cap, self.d) if self.dtype == "u8" else t.view(torch.float32).view(self.n_cap, self.d)
+
+    def _qcheck(self, X: torch.Tensor):
+        want = torch.uint8 if self.dtype == "u8" else torch.float32
+        if X.dtype != want or X.dim() != 2 or X.shape[1] != self.d or X.device != self.device:
+            raise ValueError(f"expected a {want} [m, {self.d}] tensor on {self.device}")
+        return X.contiguous()
+
+    # ------------------------------------------------------------ operations
+    def build(self, X: torch.Tensor, stream=None) -> None:
+        X = self._qcheck(X)
+        L.check(L.load().svf_build(self._h, _ptr(X), X.shape[0], _stream(stream)))
+        self.n_used = X.shape[0]
+
+    def attach(self, X: torch.Tensor, graph: torch.Tensor, deleted=None) -> None:
+        """Load an index built elsewhere (vectors, graph rows, deleted ids)."""
+        X = self._qcheck(X)
+        n = X.shape[0]
+        self.vectors()[:n].copy_(X)
+        g = graph.to(self.device, torch.int32) if graph.dtype != torch.int32 else graph.to(self.device)
+        self.graph[:n].copy_(g)
+        self.del_bits.zero_()
+        if deleted is not None and len(deleted):
+            import numpy as np
+            bits = np.zeros((self.n_cap + 31) // 32, dtype=np.uint32)
+            for i in np.asarray(deleted, dtype=np.int64):
+                bits[i >> 5] |= np.uint32(1 << (int(i) & 31))
+            self.del_bits.copy_(torch.from_numpy(bits.view(np.int32)))
+        lib = L.load()
+        if self.params.lowp & 1:
+            L.check(lib.svf_encode_bf16(_ptr(X), n, self.d, _ptr(self.vecs_bf16), _stream()))
+        if self.params.lowp & 2:
+            L.check(lib.svf_encode_fp8(_ptr(X), n, self.d, _ptr(self.vecs_fp8), (self.d + 4 + 31) // 32 * 32,
+                                       _stream()))
+        torch.cuda.synchronize(self.device)
+        L.check(lib.svf_attach(self._h, n))
+        self.n_used = n
+
+    def search(self, Q: torch.Tensor, cfg: SearchConfig, out_ids=None, out_dist=None, stream=None, qkeys=None,
+               trace_feat=None, trace_meta=None, pool_out=None):
+        Q = self._qcheck(Q)
+        nq = Q.shape[0]
+        if out_ids is None:
+            out_ids = torch.empty((nq, cfg.k), dtype=torch.int32, device=self.device)
+        if out_dist is None:
+            out_dist = torch.empty((nq, cfg.k), dtype=torch.int32 if self.dtype == "u8" else torch.float32,
+                                   device=self.device)
+        prec = {None: L.U8 if self.dtype == "u8" else L.F32, "bf16": L.BF16, "fp8": L.FP8}[cfg.precision]
+        import math
+        z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
+        sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
+                            cfg.hash_log2, _ptr(qkeys), cfg.seed, _ptr(trace_feat), _ptr(trace_meta), _ptr(pool_out))
+        L.check(L.load().svf_search(self._h, _ptr(Q), nq, C.byref(sp), _ptr(out_ids), _ptr(out_dist),
+                                    _stream(stream)))
+        return out_ids, out_dist
+
+    def insert(self, X: torch.Tensor, L_ins: int = 64, T_ins: int = 32, stream=None) -> torch.Tensor:
+        X = self._qcheck(X)
+        ids = torch.empty(X.shape[0], dtype=torch.int32, device=self.device)
+        L.check(L.load().svf_insert(self._h, _ptr(X), X.shape[0], L_ins, T_ins, _ptr(ids), _stream(stream)))
+        self.n_used += X.shape[0]
+        return ids
+
+    def delete(self, ids: torch.Tensor, stream=None) -> int:
+        ids = ids.to(self.device, torch.int32).contiguous()
+        newly = torch.zeros(1, dtype=torch.int64, device=self.device)
+        L.check(L.load().svf_delete(self._h, _ptr(ids), ids.numel(), _ptr(newly), _stream(stream)))
+        return int(newly.item())
+
+    def sync(self) -> None:
+        L.check(L.load().svf_sync(self._h))
+
+    def stats(self) -> dict:
+        c = L.Counters()
+        L.check(L.load().svf_stats(self._h, C.byref(c)))
+        return {f: getattr(c, f) for f, _ in L.Counters._fields_}
+
+    def stats_reset(self) -> None:
+        L.check(L.load().svf_stats_reset(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            L.load().svf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def knn(X: torch.Tensor, Q: torch.Tensor, k: int, metric: str = "l2", self_ids: torch.Tensor | None = None,
+        stream=None):
+    """Exact brute-force kNN on the GPU (ground truth)."""
+    lib = L.load()
+    dt = L.U8 if X.dtype == torch.uint8 else L.F32
+    X = X.contiguous()
+    Q = Q.contiguous()
+    nq = Q.shape[0]
+    work = torch.empty((nq, k), dtype=torch.int64, device=X.device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((nq, k), dtype=torch.int32 if dt == L.U8 else torch.float32, device=X.device)
+    L.check(lib.svf_knn(_ptr(X), X.shape[0], X.shape[1], dt, L.IP if metric == "ip" else L.L2, _ptr(Q), nq,
+                        _ptr(self_ids), k, _ptr(work), _ptr(ids), _ptr(dist), _stream(stream)))
+    return ids, dist
