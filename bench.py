@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Search throughput at recall@10 >= 0.95 on the 10M x 96 inner-product workload.
+
+Workload ("unit96-10M"): n = 10,000,000 unit-normalised fp32 vectors, d = 96,
+a 4,096-component Gaussian mixture of low intrinsic dimension (synth), inner
+product; out-degree R = 32; 10,000 queries per step, k = 10.  The index
+keeps fp32, bfloat16 and FP8-E4M3 (+ per-vector scale) copies of the vectors.
+Its graph is built on the GPU: an exact 2R-NN + prune build of the first
+200,000 vectors, then batched inserts of the rest (Sec. 5.1 insert path).
+
+Forms compared (each at the cheapest swept (L, T) reaching recall@10 >= 0.95
+against exact ground truth): plain FP32 traversal; BF16 / FP8 traversal with
+an exact FP32 re-rank of the final pool; the same with the learned early stop
+(trained here on traces of 200,000 training queries).  `value` is the QPS of
+the fastest form; one step = one search launch over the 10,000-query batch.
+
+`--impl reference` times the CPU oracle (FP64, all host cores) on a bounded
+sample of the same batch, same graph, same (L, T).
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+K = 10
+R = 32
+N_BOOT = 200_000
+MAX_BATCH = 1_000_000
+ROW_BYTES = {"f32": 384, "bf16": 192, "fp8": 100}  # bytes of one row's values (+ FP8 scale)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--ntrain", type=int, default=200_000)
+    ap.add_argument("--target", type=float, default=0.95)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- setup
+def build_index(svf, torch, X, log_t):
+    n = X.shape[0]
+    ix = svf.Index(96, n, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"), max_batch=MAX_BATCH)
+    n0 = min(N_BOOT, n)
+    t = time.time()
+    ix.build(torch.from_numpy(X[:n0]).cuda())
+    torch.cuda.synchronize()
+    log_t("bootstrap build", n0, time.time() - t)
+    t = time.time()
+    while ix.n_used < n:
+        b = min(ix.n_used, MAX_BATCH, n - ix.n_used)
+        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=64, T_ins=48)
+    torch.cuda.synchronize()
+    log_t("inserts", n - n0, time.time() - t)
+    return ix
+
+
+def time_search(torch, ix, Q, cfg, reps=3):
+    ix.search(Q, cfg)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ix.search(Q, cfg)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return min(ts)
+
+
+def sweep(torch, ix, Q, gt, forms, grid, target, learned):
+    from paper_2601_08528_b300.learned import recall_at_k
+    pts = []
+    for name, base in forms:
+        for L, T in grid:
+            cfg = dataclasses.replace(base, L=L, T=T)
+            if name.endswith("+stop"):
+                net = learned.get(cfg.precision)
+                if net is None or net.tau >= 1.0:
+                    continue
+                cfg = dataclasses.replace(cfg, mlp=net.packed, tau=net.tau, t_min=net.t_min)
+            ids, _ = ix.search(Q, cfg)
+            rec = recall_at_k(ids, gt)
+            sec = time_search(torch, ix, Q, cfg)
+            pts.append({"form": name, "L": L, "T": T, "recall": rec, "qps": Q.shape[0] / sec, "cfg": cfg})
+            log(f"  {name:14s} L={L:3d} T={T:3d} recall={rec:.4f} qps={Q.shape[0] / sec:,.0f}")
+    best = {}
+    for p in pts:
+        if p["recall"] >= target and (p["form"] not in best or p["qps"] > best[p["form"]]["qps"]):
+            best[p["form"]] = p
+    return pts, best
+
+
+def train_stops(torch, svf, ix, Qtr, gt_cal, ncal, precisions, L, T):
+    from paper_2601_08528_b300 import learned
+    nets = {}
+    for prec in precisions:
+        cfg = svf.SearchConfig(k=K, L=L, T=T, precision=prec, rerank=prec is not None)
+        feat, meta = learned.capture_traces(ix, Qtr[ncal:], cfg)
+        ids = learned.sample_ids(meta, T)
+        net = learned.train(feat, meta, T, ids, epochs=2, batch=4096, lr=3e-3, seed=11)
+        del feat
+        tau, r0, r1 = learned.calibrate(ix, net, Qtr[:ncal], gt_cal, cfg)
+        net.tau = tau
+        nets[prec] = net
+        log(f"  stop net for {prec}: loss={net.loss:.4f} samples={ids.numel()} tau={tau} "
+            f"recall fixed={r0:.4f} stop={r1:.4f}")
+    return nets
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, dev_index=0):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9 or c[0] != str(dev_index):
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx = float(c[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def oracle_qps(X, graph_np, Q, L, T, seconds):
+    import oracle as orc
+    st = orc.Store.from_vectors(X, "ip")
+    n = X.shape[0]
+    m = 16
+    t = time.time()
+    orc.search(st, n, graph_np, None, Q[:m], K, L, T, 0x5F0C)
+    dt = time.time() - t
+    m2 = int(min(Q.shape[0], max(m, seconds / max(dt / m, 1e-6))))
+    t = time.time()
+    orc.search(st, n, graph_np, None, Q[:m2], K, L, T, 0x5F0C)
+    dt = time.time() - t
+    return m2 / dt, m2, orc.threads()
+
+
+# ---------------------------------------------------------------- main
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if a.impl == "reference" and rank != 0:
+        return 0
+    import paper_2601_08528_b300 as svf
+    from paper_2601_08528_b300 import learned as lrn
+
+    t0 = time.time()
+
+    def log_t(*x):
+        log(f"[{time.time() - t0:7.1f}s]", *x)
+
+    X = synth.sample_chunked("unit96", a.n, 300)
+    Qe_np = synth.sample_chunked("unit96", a.nq, 302 + rank)
+    log_t("data", X.shape)
+    ix = build_index(svf, torch, X, log_t)
+    Xd = ix.vectors()[:a.n]
+    Qe = torch.from_numpy(Qe_np).cuda()
+    gt, _ = svf.knn(Xd, Qe, K, "ip")
+    torch.cuda.synchronize()
+    log_t("ground truth")
+
+    grid = [(64, 32), (64, 64), (128, 48), (128, 64), (128, 96), (128, 128), (256, 96), (256, 128), (256, 192)]
+    if a.impl == "reference":
+        # the oracle on the plain form's operating point
+        base = [("fp32", svf.SearchConfig(k=K))]
+        _, best = sweep(torch, ix, Qe, gt, base, grid, a.target, {})
+        op = best.get("fp32") or {"L": 256, "T": 192}
+        g_np = ix.graph[:a.n].cpu().numpy().view(np.uint32)
+        steps = []
+        m_used, cores = 0, 0
+        for s in range(a.warmup + a.steps):
+            q, m_used, cores = oracle_qps(X, g_np, Qe_np, op["L"], op["T"], a.cpu_seconds / max(1, a.steps))
+            if s >= a.warmup:
+                steps.append(q)
+        v = statistics.median(steps)
+        sample = f"{m_used} of {a.nq} queries per step, fixed-T FP64 search at L={op['L']} T={op['T']} on the GPU-built graph"
+        out = {"impl": "reference", "metric": "search QPS at recall@10>=0.95", "value": v, "unit": "queries/s",
+               "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "unit96-10M", "n": a.n, "d": 96, "R": R, "nq": a.nq, "k": K, "L": op["L"],
+                          "T": op["T"], "form": "fp32", "l2": "inputs larger than L2"},
+               "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
+               "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return 0
+
+    # learned stop: traces of the plain search of training queries
+    Qtr = torch.from_numpy(synth.sample_chunked("unit96", a.ntrain, 401)).cuda()
+    ncal = a.ntrain // 10
+    gt_cal, _ = svf.knn(Xd, Qtr[:ncal], K, "ip")
+    nets = train_stops(torch, svf, ix, Qtr, gt_cal, ncal, ["bf16", "fp8"], 128, 128)
+    del Qtr
+    log_t("stop networks")
+    forms = [("fp32", svf.SearchConfig(k=K)),
+             ("bf16+rerank", svf.SearchConfig(k=K, precision="bf16", rerank=True)),
+             ("fp8+rerank", svf.SearchConfig(k=K, precision="fp8", rerank=True)),
+             ("bf16+rerank+stop", svf.SearchConfig(k=K, precision="bf16", rerank=True)),
+             ("fp8+rerank+stop", svf.SearchConfig(k=K, precision="fp8", rerank=True))]
+    pts, best = sweep(torch, ix, Qe, gt, forms, grid, a.target, nets)
+    log_t("sweep")
+    if not best:
+        raise SystemExit("no form reached the recall target")
+    lowp = {k: v for k, v in best.items() if k != "fp32"}
+    win = max(lowp.values() if lowp else best.values(), key=lambda p: p["qps"])
+    cfg = win["cfg"]
+
+    # ---- timed region: `steps` launches of the winning form
+    st = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        ix.search(Qe, cfg)
+    torch.cuda.synchronize()
+    ix.stats_reset()
+    clocks = Clocks()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    ids_out = torch.empty((a.nq, K), dtype=torch.int32, device="cuda")
+    d_out = torch.empty((a.nq, K), dtype=torch.float32, device="cuda")
+    for e0, e1 in evs:
+        e0.record(st)
+        ix.search(Qe, cfg, out_ids=ids_out, out_dist=d_out)
+        e1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per = [e0.elapsed_time(e1) / 1e3 for e0, e1 in evs]
+    total = sum(per)
+    if dist:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    s = ix.stats()
+    # ---- end to end: pinned host queries in, results out, every step
+    Qh = torch.from_numpy(Qe_np).pin_memory()
+    ids_h = torch.empty((a.nq, K), dtype=torch.int32).pin_memory()
+    d_h = torch.empty((a.nq, K), dtype=torch.float32).pin_memory()
+    Qd = torch.empty_like(Qe)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        Qd.copy_(Qh, non_blocking=True)
+        ix.search(Qd, cfg, out_ids=ids_out, out_dist=d_out)
+        ids_h.copy_(ids_out, non_blocking=True)
+        d_h.copy_(d_out, non_blocking=True)
+    e1.record(st)
+    e1.synchronize()
+    e2e_t = e0.elapsed_time(e1) / 1e3
+    clk = clocks.stop(torch.cuda.current_device())
+
+    # ---- roofline of the search kernel (the only launch of a step)
+    nq = a.nq
+    form = win["form"]
+    row_b = ROW_BYTES["bf16" if form.startswith("bf16") else "fp8" if form.startswith("fp8") else "f32"]
+    iters, evals = s["search_iters"] / a.steps, s["search_evals"] / a.steps
+    alg = iters * R * 4 + evals * row_b + nq * (96 * 4 + K * 8)
+    if cfg.rerank:
+        alg += nq * cfg.L * 384
+    mean_launch = total / a.steps
+    peaks, src = measured_peaks()
+    achieved = alg / mean_launch / 1e9
+    out = {
+        "metric": "search QPS at recall@10>=0.95 (plain FP32 vs BF16/FP8 + learned stop)",
+        "value": world * nq * a.steps / total,
+        "unit": "queries/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": form.split("+")[0],
+        "data": "synthetic",
+        "config": {"workload": "unit96-10M", "n": a.n, "d": 96, "R": R, "nq": nq, "k": K, "form": form,
+                   "L": cfg.L, "T": cfg.T, "tau": getattr(cfg, "tau", None) if cfg.mlp is not None else None,
+                   "recall@10": win["recall"], "l2": "inputs larger than L2 (3.8 GB store, 1.3 GB graph)",
+                   "graph": f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins=64, T_ins=48)"},
+        "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "L": v["L"], "T": v["T"]} for k, v in best.items()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                     "alg_bytes_per_launch": alg, "iters_per_launch": iters, "evals_per_launch": evals,
+                     "hash_resets": s["hash_resets"]},
+        "e2e": {"value": world * nq * a.steps / e2e_t, "unit": "queries/s",
+                "h2d_bytes_per_step": Qh.numel() * 4, "d2h_bytes_per_step": ids_h.numel() * 4 + d_h.numel() * 4},
+        "gpu_launches": a.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        # oracle timed on host cores: fixed-T FP64 search at the fp32 operating point
+        fp = best.get("fp32", {"L": 256, "T": 192})
+        g_np = ix.graph[:a.n].cpu().numpy().view(np.uint32)
+        qps, m, cores = oracle_qps(X, g_np, Qe_np, fp["L"], fp["T"], a.cpu_seconds)
+        out["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{m} queries, FP64 fixed-T search at L={fp['L']} T={fp['T']} "
+                                         f"(the fp32 form's operating point) on the same graph"}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -218,6 +218,31 @@ int svf_encode_fp8(const float *X, int64_t n, int32_t d, void *out, int64_t pitc
 int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, const void *Q, int64_t nq,
             const int64_t *self, int32_t k, uint64_t *work_keys, uint32_t *out_ids, void *out_dist, void *stream);
 
+/* ---- learned early stop (16 -> 64 ReLU -> 1; not in the paper: an added
+ * learned part that shortens Alg. 1's fixed iteration count).
+ * Parameter vector (fp32, SVF_MLP_PARAMS entries): W1[64][16] row-major,
+ * b1[64], w2[64], b2.  The search reads the packed bf16 copy
+ * (SVF_MLP_PACKED entries, same order, zero padded). */
+#define SVF_MLP_PARAMS 1153
+#define SVF_MLP_PACKED 1160
+
+/* Minibatch gradient of the mean binary cross-entropy.  feat: device trace
+ * [nq][T][16] float; meta: device [nq][2] int32 (iterations run, last top-k
+ * change); idx: device [B] int32 sample ids q*T+t (t < iterations run);
+ * label = (t >= last change).  grad: device [SVF_MLP_PARAMS]; partial:
+ * device scratch of svf_mlp_partial_floats(B) floats; loss: device float
+ * (may be NULL).  Deterministic (fixed reduction order). */
+int svf_mlp_grad(const float *feat, const int32_t *meta, int32_t T, const int32_t *idx, int64_t B, const float *params,
+                 float *grad, float *partial, float *loss, void *stream);
+int64_t svf_mlp_partial_floats(int64_t B);
+/* One Adam step (bias-corrected, step >= 1) on device fp32 vectors. */
+int svf_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t step, float lr, float beta1,
+                 float beta2, float eps, void *stream);
+/* fp32 parameters -> packed bf16 (round to nearest even) for svf_search. */
+int svf_mlp_pack(const float *params, void *packed, void *stream);
+/* Logits of the fp32 network for n feature rows (device [n][16] -> [n]). */
+int svf_mlp_forward(const float *params, const float *feat, int64_t n, float *z, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

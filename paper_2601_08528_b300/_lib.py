@@ -17,11 +17,13 @@ EMPTY = 0xFFFFFFFF
 F32, U8, BF16, FP8 = 0, 1, 2, 3
 L2, IP = 0, 1
 PRUNE_RNG, PRUNE_RANK = 0, 1
+MLP_PARAMS, MLP_PACKED = 1153, 1160
 
 # every symbol include/svf.h declares
 SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "svf_attach", "svf_build", "svf_search",
            "svf_insert", "svf_delete", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
-           "svf_encode_fp8", "svf_knn"]
+           "svf_encode_fp8", "svf_knn", "svf_mlp_grad", "svf_mlp_partial_floats", "svf_mlp_adam", "svf_mlp_pack",
+           "svf_mlp_forward"]
 
 
 class Params(C.Structure):
@@ -88,6 +90,11 @@ def load() -> C.CDLL:
         "svf_encode_bf16": (I32, [P, I64, I32, P, P]),
         "svf_encode_fp8": (I32, [P, I64, I32, P, I64, P]),
         "svf_knn": (I32, [P, I64, I32, I32, I32, P, I64, P, I32, P, P, P, P]),
+        "svf_mlp_grad": (I32, [P, P, I32, P, I64, P, P, P, P, P]),
+        "svf_mlp_partial_floats": (I64, [I64]),
+        "svf_mlp_adam": (I32, [P, P, P, P, I64, C.c_float, C.c_float, C.c_float, C.c_float, P]),
+        "svf_mlp_pack": (I32, [P, P, P]),
+        "svf_mlp_forward": (I32, [P, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "svf_internal.h"
+#include "svf_mlp.h"
 #include "svf_update.h"
 
 using namespace svf;
@@ -85,6 +86,15 @@ WsLayout ws_layout(const svf_params &p, int64_t max_batch) {
     return w;
 }
 
+// Lanes per row when distances are computed from staged rows: the smallest
+// power of two that leaves at most 4 chunks of 16 bytes per lane.
+void set_team(RowDesc &r) {
+    int ts = 1;
+    while (ts < 32 && (r.nchunk + ts - 1) / ts > 4) ts <<= 1;
+    r.ts = ts;
+    r.cpl = (r.nchunk + ts - 1) / ts;
+}
+
 int check_params(const svf_params *p) {
     if (!p) return fail(SVF_EINVAL, "null params");
     if (p->d < 16 || p->d > 2048 || p->d % 16) return fail(SVF_EINVAL, "d=%d: need 16..2048, multiple of 16", p->d);
@@ -118,6 +128,8 @@ struct svf_index {
         r.d = p.d;
         r.dtype = p.dtype;
         r.metric = p.metric;
+        r.copy_bytes = (int)r.pitch;
+        set_team(r);
         return r;
     }
     RowDesc lowp(int which) const {
@@ -129,12 +141,15 @@ struct svf_index {
             r.pitch = (int64_t)p.d * 2;
             r.nchunk = p.d / 8;
             r.dtype = SVF_BF16;
+            r.copy_bytes = 2 * p.d;
         } else {
             r.base = reinterpret_cast<const uint8_t *>(b.vecs_fp8);
             r.pitch = fp8_pitch(p.d);
             r.nchunk = p.d / 16;
             r.dtype = SVF_FP8;
+            r.copy_bytes = (p.d + 4 + 15) / 16 * 16;
         }
+        set_team(r);
         return r;
     }
 };
@@ -486,6 +501,8 @@ int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, 
     a.X.d = d;
     a.X.dtype = dtype;
     a.X.metric = metric;
+    a.X.copy_bytes = (int)a.X.pitch;
+    set_team(a.X);
     a.n = n;
     a.Q = Q;
     a.q_row_bytes = (int)a.X.pitch;
@@ -496,6 +513,35 @@ int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, 
     a.out_keys = work_keys;
     CUDA_TRY(launch_knn(a, st));
     CUDA_TRY(launch_keys_to_out(work_keys, nq, k, k, dtype, metric, out_ids, reinterpret_cast<uint32_t *>(out_dist), st));
+    return SVF_OK;
+}
+
+int svf_mlp_grad(const float *feat, const int32_t *meta, int32_t T, const int32_t *idx, int64_t B, const float *params,
+                 float *grad, float *partial, float *loss, void *stream) {
+    if (!feat || !meta || !idx || !params || !grad || !partial || B < 1 || T < 1)
+        return fail(SVF_EINVAL, "bad arguments");
+    CUDA_TRY(launch_mlp_grad(feat, meta, T, idx, B, params, grad, partial, loss, (cudaStream_t)stream));
+    return SVF_OK;
+}
+
+int64_t svf_mlp_partial_floats(int64_t B) { return B < 1 ? 0 : (int64_t)mlp_grad_partial_floats(B); }
+
+int svf_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t step, float lr, float beta1,
+                 float beta2, float eps, void *stream) {
+    if (!params || !grad || !m || !v || step < 1) return fail(SVF_EINVAL, "bad arguments");
+    CUDA_TRY(launch_mlp_adam(params, grad, m, v, step, lr, beta1, beta2, eps, (cudaStream_t)stream));
+    return SVF_OK;
+}
+
+int svf_mlp_pack(const float *params, void *packed, void *stream) {
+    if (!params || !packed) return fail(SVF_EINVAL, "bad arguments");
+    CUDA_TRY(launch_mlp_pack(params, packed, (cudaStream_t)stream));
+    return SVF_OK;
+}
+
+int svf_mlp_forward(const float *params, const float *feat, int64_t n, float *z, void *stream) {
+    if (n < 0 || (n > 0 && (!params || !feat || !z))) return fail(SVF_EINVAL, "bad arguments");
+    CUDA_TRY(launch_mlp_forward(params, feat, n, z, (cudaStream_t)stream));
     return SVF_OK;
 }
 

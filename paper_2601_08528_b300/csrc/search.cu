@@ -1,410 +1,39 @@
-// search.cu -- batched greedy beam search over the fixed out-degree graph
-// (SVFusion Alg. 1, Sec. 4.2), one warp per query, for sm_103a.
-//
-// Per warp: the query and a visited table live in shared memory; the
-// candidate pool (L keys, sorted by (distance, id)) lives in registers,
-// L/32 keys per lane.  Each iteration picks the nearest unexpanded pool
-// entry (ballots), loads its R-entry graph row with one coalesced load,
-// drops empty / deleted / visited ids (bitset + shared-memory hash insert),
-// evaluates the survivors with teams of 8 lanes (128-bit row loads, shuffle
-// reduction), bitonic-sorts them and merges them into the pool.
-//
-// Visited table: exact open addressing while it has room; when it is half
-// full it is cleared and re-seeded with the current pool.  Forgetting an id
-// that left the pool cannot change the result: the pool's L-th key never
-// rises, so a re-evaluated id that was once rejected is rejected again.
-#include <cstdint>
-
-#include "svf_dev.cuh"
+// search.cu -- launch of the warp-per-query search kernel (search_kernel.cuh):
+// picks the instantiation for the traversal dtype, out-degree R, pool size L
+// and whether the learned-stop / trace features are needed.
 #include "svf_internal.h"
 
 namespace svf {
 
-// Stop-network inference (16 -> 64 relu -> 1) in the packed device layout:
-// W1 [64][16] bf16, b1 [64] bf16, w2 [64] bf16, b2 bf16 (see mlp.cu).
-struct MlpView {
-    const __nv_bfloat16 *W1, *b1, *w2, *b2;
-};
+cudaError_t launch_search_f32(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st);
+cudaError_t launch_search_u8(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st);
+cudaError_t launch_search_bf16(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st);
+cudaError_t launch_search_fp8(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st);
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t id, int bits) { return (id * 0x9E3779B1u) >> (32 - bits); }
-
-// Insert id; true if it was not present.  The table is kept at most half
-// full, so the probe always ends; the bound is only a guard.
-__device__ __forceinline__ bool ht_insert(uint32_t *ht, int bits, uint32_t id) {
-    const uint32_t mask = (1u << bits) - 1u;
-    uint32_t h = hash_slot(id, bits);
-    for (uint32_t p = 0; p <= mask; p++) {
-        uint32_t old = atomicCAS(ht + h, kEmpty, id);
-        if (old == kEmpty) return true;
-        if (old == id) return false;
-        h = (h + 1) & mask;
-    }
-    return false;
-}
-__device__ __forceinline__ bool ht_contains(const uint32_t *ht, int bits, uint32_t id) {
-    const uint32_t mask = (1u << bits) - 1u;
-    uint32_t h = hash_slot(id, bits);
-    for (uint32_t p = 0; p <= mask; p++) {
-        uint32_t v = ht[h];
-        if (v == id) return true;
-        if (v == kEmpty) return false;
-        h = (h + 1) & mask;
-    }
-    return false;
+size_t search_stage_bytes(const SearchArgs &a, int R) {
+    size_t cap = (size_t)R * a.trav.copy_bytes;
+    if (a.rerank && cap < (size_t)16 * a.prim.copy_bytes) cap = (size_t)16 * a.prim.copy_bytes;
+    return cap;
 }
 
-template <int LW>
-__device__ __forceinline__ void ht_reset(uint32_t *ht, int bits, const uint64_t (&pool)[LW], int lane) {
-    for (int i = lane; i < (1 << bits); i += 32) ht[i] = kEmpty;
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < LW; s++)
-        if (!key_is_pad(pool[s])) ht_insert(ht, bits, key_id(pool[s]));
-    __syncwarp();
-}
-
-// Per-iteration features of the learned stop (definitions in the oracle).
-struct FeatState {
-    float d1_0, s0, ema;
-    int t_last;
-};
-
-template <int LW>
-__device__ __forceinline__ float pool_dist(const uint64_t (&pool)[LW], int e, int dtype, int metric) {
-    uint64_t k = shfl64(pool[0], e & 31);
-#pragma unroll
-    for (int s = 1; s < LW; s++)
-        if ((e >> 5) == s) k = shfl64(pool[s], e & 31);
-    uint32_t v = key_to_out((uint32_t)(k >> 32), dtype, metric);
-    return dtype == SVF_U8 ? (float)(int32_t)v : __uint_as_float(v);
-}
-
-template <int DT, int R, int LW>
-__global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchArgs a) {
-    constexpr int L = 32 * LW;
-    constexpr int S = R / 32;  // graph ids per lane
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + wib;
-    if (qi >= a.nq) return;
-
-    uint8_t *my = smem + (size_t)wib * a.warp_smem;
-    float *qf = reinterpret_cast<float *>(my);
-    uint8_t *qb = my;
-    uint32_t *ht = reinterpret_cast<uint32_t *>(my + a.q_bytes);
-    uint32_t *list = ht + (1 << a.hash_bits);
-    uint64_t *keys = reinterpret_cast<uint64_t *>(list + a.list_len);
-
-    // ---- query to shared memory, query key
-    const uint8_t *qsrc = reinterpret_cast<const uint8_t *>(a.Q) + qi * a.q_row_bytes;
-    for (int c = lane; c < a.q_row_bytes / 16; c += 32)
-        reinterpret_cast<uint4 *>(my)[c] = __ldg(reinterpret_cast<const uint4 *>(qsrc) + c);
-    uint64_t qkey;
-    if (a.qkeys) {
-        qkey = a.qkeys[qi];
-    } else {
-        qkey = 0;
-        const uint32_t *w = reinterpret_cast<const uint32_t *>(qsrc);
-        for (int i = lane; i < a.q_row_bytes / 4; i += 32) qkey += splitmix64(((uint64_t)i << 32) | __ldg(w + i));
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) qkey += shfl64_xor(qkey, m);
-    }
-    for (int i = lane; i < (1 << a.hash_bits); i += 32) ht[i] = kEmpty;
-    __syncwarp();
-
-    // ---- InitCandidatePool: the first L distinct live ids of the draw sequence
-    const uint64_t base = splitmix64(a.seed ^ splitmix64(qkey));
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    int np = 0;
-    const int ndraw = 4 * L;
-    for (int j0 = 0; j0 < ndraw && np < L && a.n_used > 0; j0 += 32) {
-        const int j = j0 + lane;
-        uint32_t id = (uint32_t)(splitmix64(base ^ (uint64_t)j) % (uint64_t)a.n_used);
-        bool ok = j < ndraw && !is_deleted(a.del, id);
-        uint32_t m = __match_any_sync(kFull, ok ? id : kEmpty);
-        bool first = ok && ((m & lt_mask) == 0);
-        bool acc = first && !ht_contains(ht, a.hash_bits, id);
-        uint32_t b = __ballot_sync(kFull, acc);
-        int rank = __popc(b & lt_mask);
-        if (acc && np + rank < L) {
-            ht_insert(ht, a.hash_bits, id);
-            list[np + rank] = id;
-        }
-        np += min(__popc(b), L - np);
-        __syncwarp();
-    }
-    int hcount = np;
-    dist_list<DT>(a.trav, list, np, keys, 0u, lane, qf, qb);
-    __syncwarp();
-    uint64_t pool[LW];
-#pragma unroll
-    for (int s = 0; s < LW; s++) {
-        int e = s * 32 + lane;
-        pool[s] = e < np ? keys[e] : kPad;
-    }
-    warp_sort<LW>(pool, lane);
-
-    // learned stop / trace state
-    const bool learn = a.mlp != nullptr || a.trace_feat != nullptr;
-    FeatState fs{0.f, 1.f, 0.f, -1};
-    if (learn) {
-        float d1 = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
-        float dl = pool_dist<LW>(pool, max(np - 1, 0), a.out_dtype, a.trav.metric);
-        fs.d1_0 = d1;
-        fs.s0 = (dl - d1 > 0.f) ? dl - d1 : 1.f;
-    }
-
-    int iters = 0, evals = np, resets = 0, ran = 0;
-    const int reset_at = (1 << (a.hash_bits - 1)) - R;
-    for (int t = 0; t < a.T; t++) {
-        if (hcount > reset_at) {
-            ht_reset<LW>(ht, a.hash_bits, pool, lane);
-            hcount = 0;
-#pragma unroll
-            for (int s = 0; s < LW; s++) hcount += __popc(__ballot_sync(kFull, !key_is_pad(pool[s])));
-            resets++;
-        }
-        // GetNearest: the first unexpanded entry in (distance, id) order
-        int ps = -1, pl = 0;
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            uint32_t b = __ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0);
-            if (ps < 0 && b) {
-                ps = s;
-                pl = __ffs(b) - 1;
-            }
-        }
-        if (ps < 0) break;  // nothing left to expand: the pool stays unchanged
-        uint32_t pid = 0;
-        uint64_t pkey = 0;
-#pragma unroll
-        for (int s = 0; s < LW; s++)
-            if (s == ps) {
-                pkey = shfl64(pool[s], pl);
-                if (lane == pl) pool[s] |= kExpBit;
-            }
-        pid = key_id(pkey);
-        iters++;
-
-        // FetchNeighbors + filter
-        const uint32_t *row = a.graph + (int64_t)pid * R;
-        uint32_t nb[S];
-        bool fresh[S];
-#pragma unroll
-        for (int s = 0; s < S; s++) nb[s] = __ldg(row + s * 32 + lane);
-        int nf = 0;
-#pragma unroll
-        for (int s = 0; s < S; s++) {
-            uint32_t v = nb[s];
-            bool ok = v != kEmpty && (int64_t)v < a.n_used && !is_deleted(a.del, v);
-            fresh[s] = ok && ht_insert(ht, a.hash_bits, v);
-            uint32_t b = __ballot_sync(kFull, fresh[s]);
-            if (fresh[s]) list[nf + __popc(b & lt_mask)] = v;
-            nf += __popc(b);
-        }
-        hcount += nf;
-        evals += nf;
-        __syncwarp();
-        const uint32_t newflag = learn ? kNewBit : 0u;
-        dist_list<DT>(a.trav, list, nf, keys, newflag, lane, qf, qb);
-        __syncwarp();
-
-        // learned-stop inputs before the merge
-        float d1_prev = 0.f, dk_prev = 0.f, dpar = 0.f;
-        const int kk_prev = min(a.k, np);
-        if (learn) {
-            d1_prev = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
-            dk_prev = pool_dist<LW>(pool, kk_prev - 1, a.out_dtype, a.trav.metric);
-            uint32_t pv = key_to_out((uint32_t)(pkey >> 32), a.out_dtype, a.trav.metric);
-            dpar = a.out_dtype == SVF_U8 ? (float)(int32_t)pv : __uint_as_float(pv);
-        }
-
-        if (nf > 0) {
-            uint64_t cand[S];
-#pragma unroll
-            for (int s = 0; s < S; s++) {
-                int e = s * 32 + lane;
-                cand[s] = e < nf ? keys[e] : kPad;
-            }
-            warp_sort<S>(cand, lane);
-            if constexpr (S <= LW) {
-                warp_merge_into<LW, S>(pool, cand, lane);
-            } else {
-                // the best L of pool and candidates only need the best L candidates
-                uint64_t head[LW];
-#pragma unroll
-                for (int s = 0; s < LW; s++) head[s] = cand[s];
-                warp_merge_into<LW, LW>(pool, head, lane);
-            }
-        }
-        np = min(np + nf, L);
-        ran = t + 1;
-
-        if (learn) {
-            // newtop: entries of the new top-k admitted in this iteration (an
-            // older entry can only move down, so these are exactly the new ids)
-            const int kk = min(a.k, np);
-            uint32_t bnew = __ballot_sync(kFull, lane < kk && ((uint32_t)pool[0] & kNewBit));
-            int newtop = __popc(bnew), admitted = 0, unexp = 0;
-#pragma unroll
-            for (int s = 0; s < LW; s++) {
-                admitted += __popc(__ballot_sync(kFull, ((uint32_t)pool[s] & kNewBit) != 0 && !key_is_pad(pool[s])));
-                unexp += __popc(__ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0));
-                pool[s] &= ~(uint64_t)kNewBit;
-            }
-            if (newtop > 0) fs.t_last = t;
-            float d1 = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
-            float dk = pool_dist<LW>(pool, kk - 1, a.out_dtype, a.trav.metric);
-            float dl = pool_dist<LW>(pool, np - 1, a.out_dtype, a.trav.metric);
-            float mine = 0.f;
-            if (lane < kk) {
-                uint32_t v = key_to_out((uint32_t)(pool[0] >> 32), a.out_dtype, a.trav.metric);
-                mine = a.out_dtype == SVF_U8 ? (float)(int32_t)v : __uint_as_float(v);
-            }
-            float sum = mine;
-#pragma unroll
-            for (int m = 16; m > 0; m >>= 1) sum += __shfl_xor_sync(kFull, sum, m);
-            const float mean = sum / kk;
-            float dev = lane < kk ? (mine - mean) * (mine - mean) : 0.f;
-#pragma unroll
-            for (int m = 16; m > 0; m >>= 1) dev += __shfl_xor_sync(kFull, dev, m);
-            const float inv = 1.f / fs.s0;
-            float f[16];
-            f[0] = (float)(t + 1) / a.T;
-            f[1] = (fs.d1_0 - d1) * inv;
-            f[2] = (dk - d1) * inv;
-            f[3] = (dl - d1) * inv;
-            f[4] = (mean - d1) * inv;
-            f[5] = sqrtf(dev / kk) * inv;
-            f[6] = (float)admitted / R;
-            f[7] = (float)unexp / L;
-            f[8] = (float)newtop / a.k;
-            f[9] = (float)(t - fs.t_last) / a.T;
-            f[10] = (float)(np - unexp) / L;
-            f[11] = (float)(ps * 32 + pl) / L;
-            f[12] = (dk_prev - dk) * inv;
-            f[13] = (d1_prev - d1) * inv;
-            f[14] = (dpar - d1) * inv;
-            fs.ema = 0.5f * fs.ema + 0.5f * f[6];
-            f[15] = fs.ema;
-            if (a.trace_feat && lane < 16) {
-                float fv = f[0];
-#pragma unroll
-                for (int i = 1; i < 16; i++)
-                    if (lane == i) fv = f[i];
-                a.trace_feat[(qi * a.T + t) * 16 + lane] = fv;
-            }
-            if (a.mlp && t + 1 >= a.t_min) {
-                // lane j computes hidden units j and j+32
-                const MlpView *mv = reinterpret_cast<const MlpView *>(a.mlp);
-                float z = 0.f;
-#pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    const int j = lane + 32 * half;
-                    float h = __bfloat162float(mv->b1[j]);
-#pragma unroll
-                    for (int i = 0; i < 16; i++) h = fmaf(__bfloat162float(mv->W1[j * 16 + i]), f[i], h);
-                    if (h > 0.f) z = fmaf(__bfloat162float(mv->w2[j]), h, z);
-                }
-#pragma unroll
-                for (int m = 16; m > 0; m >>= 1) z += __shfl_xor_sync(kFull, z, m);
-                z += __bfloat162float(*mv->b2);
-                if (z >= a.z_tau) break;
-            }
-        }
-    }
-
-    // ---- optional exact re-rank of the final pool from the primary store
-    if (a.rerank) {
-        int npool = 0;
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            bool real = !key_is_pad(pool[s]);
-            uint32_t b = __ballot_sync(kFull, real);
-            if (real) list[npool + __popc(b & lt_mask)] = key_id(pool[s]);
-            npool += __popc(b);
-        }
-        __syncwarp();
-        // the fp32 query is still in shared memory
-        if (a.prim.dtype == SVF_F32) dist_list<SVF_F32>(a.prim, list, npool, keys, 0u, lane, qf, qb);
-        __syncwarp();
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            int e = s * 32 + lane;
-            pool[s] = e < npool ? keys[e] : kPad;
-        }
-        warp_sort<LW>(pool, lane);
-    }
-
-    // ---- top-k out (k <= 32: slot 0)
-    if (lane < a.k) {
-        uint64_t k0 = pool[0];
-        bool pad = key_is_pad(k0);
-        a.out_ids[qi * a.k + lane] = pad ? kEmpty : key_id(k0);
-        a.out_dist[qi * a.k + lane] = key_to_out(pad ? 0xFFFFFFFFu : (uint32_t)(k0 >> 32), a.out_dtype, a.trav.metric);
-    }
-    if (a.pool_out) {
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            uint64_t k0 = pool[s];
-            a.pool_out[qi * L + s * 32 + lane] =
-                key_is_pad(k0) ? kPad : (k0 & ~(uint64_t)(kExpBit | kNewBit));
-        }
-    }
-    if (a.trace_meta && lane == 0) {
-        a.trace_meta[qi * 2 + 0] = ran;
-        a.trace_meta[qi * 2 + 1] = fs.t_last;
-    }
-    if (lane == 0) {
-        atomicAdd(a.status + kStQueries, 1ull);
-        atomicAdd(a.status + kStIters, (unsigned long long)iters);
-        atomicAdd(a.status + kStEvals, (unsigned long long)evals);
-        if (resets) atomicAdd(a.status + kStResets, (unsigned long long)resets);
-    }
-}
-
-template <int DT, int R>
-static cudaError_t launch_dt_r(const SearchArgs &a, int LW, size_t smem, cudaStream_t st) {
-    dim3 grid((unsigned)((a.nq + kSearchWarps - 1) / kSearchWarps)), block(kSearchWarps * 32);
-    switch (LW) {
-#define SVF_LW_CASE(X)                                                                                  \
-    case X:                                                                                             \
-        if (cudaFuncSetAttribute(search_kernel<DT, R, X>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 (int)smem) != cudaSuccess)                                             \
-            return cudaGetLastError();                                                                  \
-        search_kernel<DT, R, X><<<grid, block, smem, st>>>(a);                                          \
-        return cudaGetLastError();
-        SVF_LW_CASE(1)
-        SVF_LW_CASE(2)
-        SVF_LW_CASE(4)
-        SVF_LW_CASE(8)
-#undef SVF_LW_CASE
-    }
-    return cudaErrorInvalidValue;
-}
-
-template <int DT>
-static cudaError_t launch_dt(const SearchArgs &a, int R, int LW, size_t smem, cudaStream_t st) {
-    if (R == 32) return launch_dt_r<DT, 32>(a, LW, smem, st);
-    return launch_dt_r<DT, 64>(a, LW, smem, st);
-}
-
-size_t search_warp_smem(int d, int L, int R, int hash_bits) {
+size_t search_warp_smem(int d, int L, int R, int hash_bits, size_t stage_bytes) {
     size_t q = ((size_t)d * 4 + 15) / 16 * 16;
     size_t list = (size_t)(L > 2 * R ? L : 2 * R);
-    return q + ((size_t)4 << hash_bits) + list * 4 + list * 8;
+    return q + ((size_t)4 << hash_bits) + list * 4 + list * 8 + stage_bytes + 16;
 }
 
 cudaError_t launch_search(SearchArgs a, int R, int L, cudaStream_t st) {
     a.list_len = L > 2 * R ? L : 2 * R;
-    a.warp_smem = search_warp_smem(a.trav.d, L, R, a.hash_bits);
-    size_t smem = a.warp_smem * kSearchWarps;
+    a.stage_bytes = (uint32_t)search_stage_bytes(a, R);
+    a.warp_smem = search_warp_smem(a.trav.d, L, R, a.hash_bits, a.stage_bytes);
+    const size_t smem = a.warp_smem * kSearchWarps;
     const int LW = L / 32;
+    const bool learn = a.mlp != nullptr || a.trace_feat != nullptr;
     switch (a.trav.dtype) {
-    case SVF_F32: return launch_dt<SVF_F32>(a, R, LW, smem, st);
-    case SVF_U8: return launch_dt<SVF_U8>(a, R, LW, smem, st);
-    case SVF_BF16: return launch_dt<SVF_BF16>(a, R, LW, smem, st);
-    default: return launch_dt<SVF_FP8>(a, R, LW, smem, st);
+    case SVF_F32: return launch_search_f32(a, R, LW, learn, smem, st);
+    case SVF_U8: return launch_search_u8(a, R, LW, learn, smem, st);
+    case SVF_BF16: return launch_search_bf16(a, R, LW, learn, smem, st);
+    default: return launch_search_fp8(a, R, LW, learn, smem, st);
     }
 }
 

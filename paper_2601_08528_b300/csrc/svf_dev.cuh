@@ -153,6 +153,9 @@ struct RowDesc {
     int d;
     int dtype;            // traversal dtype
     int metric;
+    int copy_bytes;       // bytes staged per row (values, + the FP8 scale), multiple of 16
+    int ts;               // lanes per row when staged (power of two, <= 32)
+    int cpl;              // chunks per lane = ceil(nchunk / ts)
 };
 
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
@@ -388,6 +391,104 @@ enum StatusWord {
 __device__ __forceinline__ void set_error(unsigned long long *st, int code, long long detail) {
     if (atomicCAS(st + kStError, 0ull, (unsigned long long)(unsigned)(-code)) == 0ull)
         st[kStDetail] = (unsigned long long)detail;
+}
+
+}  // namespace svf
+
+namespace svf {
+
+// ---------------------------------------------------------------- staging
+// Rows are brought into a per-warp shared-memory buffer by the bulk-copy
+// (TMA, 1-D) engine: one cp.async.bulk per row, completion counted in bytes
+// on a per-warp mbarrier.  No cluster multicast is used.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr uint32_t kWaitLimit = 1u << 26;  // bounded wait on a staging barrier
+
+struct Stage {
+    uint8_t *buf;     // per-warp buffer (16-byte aligned)
+    uint32_t cap;     // bytes
+    uint64_t *mbar;   // per-warp mbarrier
+    uint32_t phase;   // parity of the next phase to wait for
+};
+
+// Distance keys of rows list[0..n) (smem ids) written to keys[0..n) with
+// `flags` or'ed into the id word.  Rows are staged in chunks that fit the
+// buffer; each chunk is one batch of bulk copies and one barrier wait.
+// Returns false if a wait gave up (the caller reports SVF_ETIMEOUT).
+template <int DT>
+__device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const uint32_t *list, int n, uint64_t *keys,
+                                            uint32_t flags, int lane, const float *qf, const uint8_t *qb) {
+    const int per = (int)(S.cap / (uint32_t)R.copy_bytes);
+    const int ts = R.ts, team = lane / ts, sub = lane % ts, nteam = 32 / ts;
+    for (int i0 = 0; i0 < n; i0 += per) {
+        const int cnt = min(per, n - i0);
+        __syncwarp();
+        fence_proxy_async();  // earlier reads of the buffer precede the new async writes
+        if (lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(cnt * R.copy_bytes));
+        __syncwarp();
+        for (int j = lane; j < cnt; j += 32)
+            bulk_g2s(S.buf + (size_t)j * R.copy_bytes, R.base + (int64_t)list[i0 + j] * R.pitch, R.copy_bytes, S.mbar);
+        uint32_t it = 0;
+        while (!mbar_try_wait(S.mbar, S.phase))
+            if (++it > kWaitLimit) return false;
+        S.phase ^= 1u;
+        for (int r0 = 0; r0 < cnt; r0 += nteam) {
+            const int r = r0 + team;
+            const bool valid = r < cnt;
+            const uint8_t *row = S.buf + (size_t)(valid ? r : 0) * R.copy_bytes;
+            float facc = 0.f, scale = 1.f;
+            uint32_t iacc = 0;
+            if (DT == SVF_FP8) scale = *reinterpret_cast<const float *>(row + R.d);
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int c = sub + u * ts;
+                if (valid && u < R.cpl && c < R.nchunk) v[u] = reinterpret_cast<const uint4 *>(row)[c];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int c = sub + u * ts;
+                if (valid && u < R.cpl && c < R.nchunk) chunk_acc<DT>(R.metric, v[u], c, qf, qb, scale, facc, iacc);
+            }
+            for (int c0 = sub + 4 * ts; c0 < R.nchunk; c0 += ts)  // rows longer than 4 chunks per lane
+                if (valid) chunk_acc<DT>(R.metric, reinterpret_cast<const uint4 *>(row)[c0], c0, qf, qb, scale, facc, iacc);
+            for (int m = ts >> 1; m > 0; m >>= 1) {
+                if constexpr (DT == SVF_U8)
+                    iacc += __shfl_xor_sync(kFull, iacc, m);
+                else
+                    facc += __shfl_xor_sync(kFull, facc, m);
+            }
+            if (valid && sub == 0) keys[i0 + r] = make_key(finish_key<DT>(R.metric, facc, iacc, scale), list[i0 + r] | flags);
+        }
+    }
+    __syncwarp();
+    return true;
 }
 
 }  // namespace svf

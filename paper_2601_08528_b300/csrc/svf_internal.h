@@ -37,10 +37,10 @@ struct SearchArgs {
     int32_t *trace_meta;
     unsigned long long *status;
     int list_len;
+    uint32_t stage_bytes;
     size_t warp_smem;
 };
 
-size_t search_warp_smem(int d, int L, int R, int hash_bits);
 cudaError_t launch_search(SearchArgs a, int R, int L, cudaStream_t st);
 
 // Brute-force exact kNN over the rows of a store (knn.cu).

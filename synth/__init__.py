@@ -9,8 +9,14 @@ shapes and value ranges of the workloads:
 * ``tiny``      n=10,000 fp32, d=128, 16 centres U[-5,5]^d, sigma=1 (L2).
 * ``u8``        n=1,000,000 uint8, d=128, 1,024 centres U[32,224]^d,
                 sigma=20, rounded half-to-even and clipped to [0,255] (L2).
-* ``unit96``    n=10,000,000 fp32, d=96 (Deep1B's dimension), 4,096 unit
-                centres, x = normalize(c + 0.05 N(0,I)) (inner product).
+* ``unit96``    n=10,000,000 fp32, d=96 (Deep1B's dimension), 4,096
+                components with a low intrinsic dimension, unit-normalised
+                (inner product): a fixed random orthonormal basis A (96 x 16),
+                component means z_c ~ N(0, I_16), x = normalize(A (z_c + u)
+                + 0.02 e) with u ~ N(0, I_16), e ~ N(0, I_96).  Real
+                descriptors such as Deep1B's have a low intrinsic dimension;
+                a mixture of 4,096 isotropic 96-d blobs would instead split
+                into thousands of disconnected neighbourhoods.
 * ``serve128``  n=50,000,000 fp32, d=128, 16,384 centres U[-5,5]^d, sigma=1.
 
 Every draw is keyed by an explicit seed so a test, the oracle and a GPU run
@@ -18,11 +24,13 @@ see byte-identical inputs.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
+import os
 
 import numpy as np
 
-__all__ = ["Mixture", "MIXTURES", "centres", "sample", "sample_chunked", "pick_live_ids", "zipf_components"]
+__all__ = ["Mixture", "MIXTURES", "centres", "latent_basis", "sample", "sample_chunked", "pick_live_ids", "zipf_components"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -37,23 +45,35 @@ class Mixture:
     sigma: float
     centre_seed: int
     normalize: bool = False
+    latent_dim: int = 0       # "latent": component means and noise live in span(A)
+    iso_sigma: float = 0.0    # "latent": isotropic noise added in the full space
 
 
 MIXTURES = {
     "tiny": Mixture("tiny", 128, 16, "f32", "uniform", -5.0, 5.0, 1.0, 101),
     "u8": Mixture("u8", 128, 1024, "u8", "uniform", 32.0, 224.0, 20.0, 201),
-    "unit96": Mixture("unit96", 96, 4096, "f32", "unit", 0.0, 0.0, 0.05, 301, normalize=True),
+    "unit96": Mixture("unit96", 96, 4096, "f32", "latent", 0.0, 0.0, 1.0, 301, normalize=True,
+                      latent_dim=16, iso_sigma=0.02),
     "serve128": Mixture("serve128", 128, 16384, "f32", "uniform", -5.0, 5.0, 1.0, 501),
 }
 
 
 def centres(mix: Mixture) -> np.ndarray:
-    """The mixture's centres, float64 [n_centres, d]."""
+    """The mixture's centres, float64 [n_centres, d] ([n_centres, r] latent
+    means for a "latent" mixture)."""
     rng = np.random.default_rng(mix.centre_seed)
     if mix.centre_kind == "uniform":
         return rng.uniform(mix.centre_lo, mix.centre_hi, size=(mix.n_centres, mix.d))
+    if mix.centre_kind == "latent":
+        return rng.standard_normal(size=(mix.n_centres, mix.latent_dim))
     c = rng.standard_normal(size=(mix.n_centres, mix.d))
     return c / np.linalg.norm(c, axis=1, keepdims=True)
+
+
+def latent_basis(mix: Mixture) -> np.ndarray:
+    """Orthonormal [d, r] basis of a "latent" mixture."""
+    rng = np.random.default_rng(mix.centre_seed + 1_000_003)
+    return np.linalg.qr(rng.standard_normal(size=(mix.d, mix.latent_dim)))[0]
 
 
 def _finish(mix: Mixture, x: np.ndarray) -> np.ndarray:
@@ -72,14 +92,19 @@ def sample(mix: Mixture | str, n: int, seed: int, labels_out: list | None = None
     c = centres(mix)
     rng = np.random.default_rng(seed)
     lab = rng.integers(0, mix.n_centres, size=n)
-    x = c[lab] + mix.sigma * rng.standard_normal(size=(n, mix.d))
+    if mix.centre_kind == "latent":
+        A = latent_basis(mix)
+        z = c[lab] + mix.sigma * rng.standard_normal(size=(n, mix.latent_dim))
+        x = z @ A.T + mix.iso_sigma * rng.standard_normal(size=(n, mix.d))
+    else:
+        x = c[lab] + mix.sigma * rng.standard_normal(size=(n, mix.d))
     if labels_out is not None:
         labels_out.append(lab)
     return _finish(mix, x)
 
 
 def sample_chunked(mix: Mixture | str, n: int, seed: int, chunk: int = 1 << 20,
-                   component_sampler=None) -> np.ndarray:
+                   component_sampler=None, workers: int | None = None) -> np.ndarray:
     """Like :func:`sample` for large n: float32 arithmetic, drawn in chunks.
 
     Chunk j uses the generator seeded by (seed, j), so the result depends
@@ -90,22 +115,42 @@ def sample_chunked(mix: Mixture | str, n: int, seed: int, chunk: int = 1 << 20,
         mix = MIXTURES[mix]
     c = centres(mix).astype(np.float32)
     out = np.empty((n, mix.d), dtype=np.uint8 if mix.dtype == "u8" else np.float32)
-    for j, s in enumerate(range(0, n, chunk)):
+    A = latent_basis(mix).astype(np.float32) if mix.centre_kind == "latent" else None
+
+    def one(j):
+        s = j * chunk
         m = min(chunk, n - s)
         rng = np.random.default_rng([seed, j])
         if component_sampler is None:
             lab = rng.integers(0, mix.n_centres, size=m)
         else:
             lab = component_sampler(rng, m)
-        x = rng.standard_normal(size=(m, mix.d), dtype=np.float32)
-        x *= np.float32(mix.sigma)
-        x += c[lab]
+        if mix.centre_kind == "latent":
+            z = rng.standard_normal(size=(m, mix.latent_dim), dtype=np.float32)
+            z *= np.float32(mix.sigma)
+            z += c[lab]
+            x = z @ A.T
+            x += np.float32(mix.iso_sigma) * rng.standard_normal(size=(m, mix.d), dtype=np.float32)
+        else:
+            x = rng.standard_normal(size=(m, mix.d), dtype=np.float32)
+            x *= np.float32(mix.sigma)
+            x += c[lab]
         if mix.normalize:
             x /= np.linalg.norm(x, axis=1, keepdims=True)
         if mix.dtype == "u8":
             out[s:s + m] = np.clip(np.rint(x), 0, 255).astype(np.uint8)
         else:
             out[s:s + m] = x
+
+    nchunk = (n + chunk - 1) // chunk
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1)
+    if workers <= 1 or nchunk == 1:
+        for j in range(nchunk):
+            one(j)
+    else:
+        with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+            list(ex.map(one, range(nchunk)))
     return out
 
 
