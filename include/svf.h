@@ -218,6 +218,25 @@ int svf_encode_fp8(const float *X, int64_t n, int32_t d, void *out, int64_t pitc
 int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, const void *Q, int64_t nq,
             const int64_t *self, int32_t k, uint64_t *work_keys, uint32_t *out_ids, void *out_dist, void *stream);
 
+/* ---- allocation-free variant of svf_knn (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc -- a plugin or custom call inside
+ * a host framework whose memory manager owns the device's memory, or a
+ * latency-critical loop where an allocation could stall -- this computes the
+ * same result as svf_knn without the caller's work_keys buffer.  Its scratch
+ * is a fixed device array of svf_knn_static_capacity() = 1,048,576 uint64
+ * keys (8 MiB) that every GPU loading the library holds until the process
+ * exits; nq * k above that capacity is rejected with SVF_EINVAL.  The first
+ * call on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.
+ * All calls share the array, which keeps the last call's keys: calls that
+ * overlap on the GPU (different streams, devices sharing nothing else) race
+ * and must be serialised by the caller.  The call allocates nothing.  Errors
+ * are described by svf_knn_static_error(). */
+int svf_knn_static(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, const void *Q, int64_t nq,
+                   const int64_t *self, int32_t k, uint32_t *out_ids, void *out_dist, void *stream);
+int64_t svf_knn_static_capacity(void);
+const char *svf_knn_static_error(void);
+
 /* ---- learned early stop (16 -> 64 ReLU -> 1; not in the paper: an added
  * learned part that shortens Alg. 1's fixed iteration count).
  * Parameter vector (fp32, SVF_MLP_PARAMS entries): W1[64][16] row-major,
