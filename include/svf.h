@@ -111,8 +111,9 @@ typedef struct {
  *   rerank    1: recompute the final pool's distances exactly from the
  *             primary store and re-sort before taking k (low precision only)
  *   mlp       device pointer to a packed stop network (svf_mlp_pack layout)
- *             or NULL; with it the query stops after iteration t once
- *             t+1 >= t_min and z >= z_tau (z = the network's logit)
+ *             or NULL; with it the network is evaluated after iteration t
+ *             when t+1 >= t_min and (t+1-t_min) % t_every == 0 (t_every 0
+ *             means 1), and the query stops there if z >= z_tau (z = logit)
  *   qkeys     device, nq uint64 query keys, or NULL: key = wrapping sum over
  *             the query's 32-bit words w_i of splitmix64((i << 32) | w_i)
  *   seed      pool-initialisation seed (0: the index's seed)
@@ -135,6 +136,8 @@ typedef struct {
     float *trace_feat;
     int32_t *trace_meta;
     uint64_t *pool_out;
+    int32_t t_every;
+    int32_t reserved0;
 } svf_search_params;
 
 /* Running counters (since svf_create or svf_stats_reset). */

@@ -72,7 +72,7 @@ def lib():
             "orc_mlp_forward": (None, [P, P, P, D, P, I64, P, P]),
             "orc_mlp_backward": (D, [P, P, P, D, P, P, I64, P, P, P, P]),
             "orc_search_ex": (None, [S, I64, P, I32, P, P, I64, P, I32, I32, I32, U64, P, P, P, P, P, P,
-                                     P, P, P, D, D, I32, P, P]),
+                                     P, P, P, D, D, I32, I32, P, P]),
             "orc_dist_ids": (None, [S, P, I64, P, I32, P]),
         }
         for name, (res, args) in sig.items():
@@ -328,7 +328,7 @@ def mlp_backward(net: MLP, F: np.ndarray, y: np.ndarray):
 
 def search_ex(store: Store, n_used: int, graph: np.ndarray, delbits, Q: np.ndarray, k: int, L: int, T: int,
               seed: int, trace: bool = False, net: MLP | None = None, tau: float = 0.5, t_min: int = 4,
-              qkeys=None):
+              qkeys=None, t_every: int = 1):
     """Search with the per-iteration trace and/or the learned stop."""
     Q = np.ascontiguousarray(Q)
     nq = Q.shape[0]
@@ -351,7 +351,7 @@ def search_ex(store: Store, n_used: int, graph: np.ndarray, delbits, Q: np.ndarr
     args = (None, None, None, 0.0) if net is None else (_p(net.W1), _p(net.b1), _p(net.w2), net.b2)
     lib().orc_search_ex(C.byref(st), n_used, _p(graph), R, _p(delbits), _p(Q), nq, _p(qk), k, L, T, seed,
                         _p(out["ids"]), _p(out["dist"]), _p(out["gap"]), _p(out.get("feat")), _p(out["n_feat"]),
-                        _p(out["t_last"]), *args, z_tau, t_min, _p(out["stop_iter"]), _p(out["margin"]))
+                        _p(out["t_last"]), *args, z_tau, t_min, t_every, _p(out["stop_iter"]), _p(out["margin"]))
     return out
 
 

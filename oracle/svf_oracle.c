@@ -35,7 +35,8 @@
  *   - "GetNearest" is the nearest *unexpanded* entry, one per iteration;
  *   - every order is lexicographic (distance, id); detour tests are strict;
  *   - L2 is squared Euclidean; inner product is scored as -<q,x>;
- *   - random initialisation draws id_j = splitmix64(base ^ j) mod n_used,
+ *   - random initialisation draws id_j = floor(hi32(splitmix64(base ^ j)) *
+ *     n_used / 2^32) (the multiply-shift range reduction of Lemire, 2019),
  *     base = splitmix64(seed ^ splitmix64(qkey)), j = 0,1,..., keeping the
  *     first L distinct live ids within 4L draws; qkey is the caller's key or
  *     the wrapping sum over the query's little-endian 32-bit words w_i of
@@ -555,14 +556,17 @@ typedef struct {
      f3 (dL - d1)/s0       f4 (mean_k - d1)/s0    f5 std_k/s0
      f6 admitted/R         f7 unexpanded/L        f8 newtop/k
      f9 (t - t_last)/T     f10 expanded/L         f11 parent rank/L
-     f12 (dk_prev - dk)/s0 f13 (d1_prev - d1)/s0  f14 (d_parent - d1)/s0
+     f12 (dk_prev - dk)/s0 f13 (d1_prev - d1)/s0  f14 (d_next - dk)/s0
      f15 e_t = (e_{t-1} + f6)/2, e_{-1} = 0
    admitted = this iteration's candidates present in the pool after the
    merge; newtop = ids of the new top-kk absent from the previous top-kk;
-   t_last = last iteration whose merge changed the top-kk set (-1 before).
+   t_last = last iteration whose merge changed the top-kk set (-1 before);
+   d_next = distance of the nearest unexpanded entry after the merge (the
+   next parent), or dL when every entry is expanded.
    mean_k / std_k: mean and population standard deviation of the top-kk.
-   The stop network is p = sigmoid(z), z = w2 . relu(W1 f + b1) + b2; the
-   search stops after iteration t when t+1 >= t_min and z >= logit(tau). */
+   The stop network is p = sigmoid(z), z = w2 . relu(W1 f + b1) + b2; it is
+   evaluated after iteration t when t+1 >= t_min and (t+1-t_min) is a
+   multiple of t_every, and the search stops there if z >= logit(tau). */
 #define NFEAT 16
 #define NHID 64
 typedef struct {
@@ -572,6 +576,7 @@ typedef struct {
     const double *W1, *b1, *w2; /* stop network (NULL: no stop) */
     double b2, z_tau;
     int32_t t_min;
+    int32_t t_every;      /* evaluate the network every t_every iterations (>= 1) */
     double margin;        /* min |z - z_tau| over evaluated iterations */
     int32_t stop_iter;    /* iterations run when stopped, -1 if never */
 } feat_ctx;
@@ -599,7 +604,7 @@ static double search_one(const orc_store *X, const srch_ctx *S, const double *q,
     /* InitCandidatePool: L distinct live ids from the draw sequence. */
     uint64_t base = splitmix64(S->seed ^ splitmix64(qkey));
     for (int64_t j = 0; j < 4 * (int64_t)L && np < L && S->n_used > 0; j++) {
-        uint32_t id = (uint32_t)(splitmix64(base ^ (uint64_t)j) % (uint64_t)S->n_used);
+        uint32_t id = (uint32_t)(((splitmix64(base ^ (uint64_t)j) >> 32) * (uint64_t)S->n_used) >> 32);
         if (is_deleted(S->del, id) || set_has(&vis, id)) continue;
         set_add(&vis, id);
         decode_row(X, id, x);
@@ -653,7 +658,6 @@ static double search_one(const orc_store *X, const srch_ctx *S, const double *q,
         int k = S->k;
         int kk_prev = np < k ? np : k;
         double d1_prev = np ? pool[0].d : 0.0, dk_prev = np ? pool[kk_prev - 1].d : 0.0;
-        double d_par = pool[p].d;
         uint32_t *old_top = F ? (uint32_t *)malloc(sizeof(uint32_t) * (kk_prev > 0 ? kk_prev : 1)) : NULL;
         for (int i = 0; F && i < kk_prev; i++) old_top[i] = pool[i].id;
         int ncand = nb - np;
@@ -700,13 +704,19 @@ static double search_one(const orc_store *X, const srch_ctx *S, const double *q,
             f[11] = (double)p / L;
             f[12] = (dk_prev - dk) / s0;
             f[13] = (d1_prev - d1) / s0;
-            f[14] = (d_par - d1) / s0;
+            double d_next = dL;
+            for (int i = 0; i < np; i++)
+                if (!pool[i].exp) {
+                    d_next = pool[i].d;
+                    break;
+                }
+            f[14] = (d_next - dk) / s0;
             ema = 0.5 * ema + 0.5 * f[6];
             f[15] = ema;
             if (F->feat) memcpy(F->feat + (int64_t)t * NFEAT, f, sizeof(f));
             F->n_feat = t + 1;
             F->t_last = t_last;
-            if (F->W1 && t + 1 >= F->t_min) {
+            if (F->W1 && t + 1 >= F->t_min && (t + 1 - F->t_min) % (F->t_every > 0 ? F->t_every : 1) == 0) {
                 double z = mlp_z(F->W1, F->b1, F->w2, F->b2, f);
                 double mg = fabs(z - F->z_tau);
                 if (mg < F->margin) F->margin = mg;
@@ -1033,13 +1043,14 @@ void orc_set_threads(int32_t t) {
    n_feat[nq] the number of rows written; t_last[nq] the last iteration that
    changed the top-k set (labels: y_t = t >= t_last).  When W1 != NULL the
    stop network (weights as given, FP64 arithmetic) ends a query after
-   iteration t once t+1 >= t_min and z >= z_tau; stop_iter[nq] = iterations
+   iteration t once t+1 >= t_min, (t+1-t_min) % t_every == 0 and z >= z_tau;
+   stop_iter[nq] = iterations
    run (-1: never stopped), margin[nq] = min |z - z_tau| seen. */
 void orc_search_ex(const orc_store *X, int64_t n_used, const uint32_t *graph, int32_t R, const uint32_t *del,
                    const void *Q, int64_t nq, const uint64_t *qkeys, int32_t k, int32_t L, int32_t T, uint64_t seed,
                    uint32_t *out_ids, double *out_d, double *out_gap, double *feat, int32_t *n_feat,
                    int32_t *t_last, const double *W1, const double *b1, const double *w2, double b2, double z_tau,
-                   int32_t t_min, int32_t *stop_iter, double *margin) {
+                   int32_t t_min, int32_t t_every, int32_t *stop_iter, double *margin) {
     srch_ctx S = {n_used, graph, R, del, L, T, k, seed};
     int d = X->d;
     int64_t qb = query_bytes(X);
@@ -1064,6 +1075,7 @@ void orc_search_ex(const orc_store *X, int64_t n_used, const uint32_t *graph, in
             F.b2 = b2;
             F.z_tau = z_tau;
             F.t_min = t_min;
+            F.t_every = t_every;
             double g = search_one(X, &S, q, key, pool, &np, &st, x, buf, &F);
             for (int i = 0; i < k; i++) {
                 out_ids[qi * k + i] = i < np ? pool[i].id : ORC_EMPTY;

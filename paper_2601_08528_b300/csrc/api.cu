@@ -302,6 +302,7 @@ static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search
     a.mlp = sp->mlp;
     a.z_tau = sp->z_tau;
     a.t_min = sp->t_min;
+    a.t_every = sp->t_every > 0 ? sp->t_every : 1;
     a.trace_feat = sp->trace_feat;
     a.trace_meta = sp->trace_meta;
     a.status = h->status();

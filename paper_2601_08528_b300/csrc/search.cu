@@ -10,9 +10,11 @@ cudaError_t launch_search_u8(const SearchArgs &a, int R, int LW, bool learn, siz
 cudaError_t launch_search_bf16(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st);
 cudaError_t launch_search_fp8(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st);
 
+// The staging buffer holds one graph row's worth of candidates; the final
+// re-rank reuses it in chunks of whole primary rows (at least 4).
 size_t search_stage_bytes(const SearchArgs &a, int R) {
     size_t cap = (size_t)R * a.trav.copy_bytes;
-    if (a.rerank && cap < (size_t)16 * a.prim.copy_bytes) cap = (size_t)16 * a.prim.copy_bytes;
+    if (a.rerank && cap < (size_t)4 * a.prim.copy_bytes) cap = (size_t)4 * a.prim.copy_bytes;
     return cap;
 }
 

@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
     const int ndraw = 4 * L;
     for (int j0 = 0; j0 < ndraw && np < L && a.n_used > 0; j0 += 32) {
         const int j = j0 + lane;
-        uint32_t id = (uint32_t)(splitmix64(base ^ (uint64_t)j) % (uint64_t)a.n_used);
+        // multiply-shift range reduction of the upper 32 random bits
+        const uint32_t id = __umulhi((uint32_t)(splitmix64(base ^ (uint64_t)j) >> 32), (uint32_t)a.n_used);
         bool ok = j < ndraw && !is_deleted(a.del, id);
         uint32_t m = __match_any_sync(kFull, ok ? id : kEmpty);
         bool first = ok && ((m & lt_mask) == 0);
@@ -154,11 +155,30 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
     // learned stop / trace state
     constexpr bool learn = LEARN;
     FeatState fs{0.f, 1.f, 0.f, -1};
+    float inv_s0 = 1.f, inv_T = 1.f, inv_k = 1.f;
+    // this lane's share of the stop network: hidden units lane and lane+32
+    uint32_t w1p[2][8] = {}, hb[2] = {};
+    float b2 = 0.f;
     if (learn) {
         float d1 = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
         float dl = pool_dist<LW>(pool, max(np - 1, 0), a.out_dtype, a.trav.metric);
         fs.d1_0 = d1;
         fs.s0 = (dl - d1 > 0.f) ? dl - d1 : 1.f;
+        inv_s0 = 1.f / fs.s0;
+        inv_T = 1.f / (float)max(a.T, 1);
+        inv_k = 1.f / (float)a.k;
+        if (a.mlp) {
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(a.mlp);  // bf16 pairs
+            const uint16_t *wh = reinterpret_cast<const uint16_t *>(a.mlp);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int j = lane + 32 * h;
+#pragma unroll
+                for (int i = 0; i < 8; i++) w1p[h][i] = __ldg(wp + j * 8 + i);
+                hb[h] = (uint32_t)__ldg(wh + kMlpOffB1 + j) | ((uint32_t)__ldg(wh + kMlpOffW2 + j) << 16);
+            }
+            b2 = __uint_as_float((uint32_t)__ldg(wh + kMlpOffB2) << 16);
+        }
     }
 
     int iters = 0, evals = np, resets = 0, ran = 0;
@@ -227,14 +247,15 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
             return;
         }
 
-        // learned-stop inputs before the merge
-        float d1_prev = 0.f, dk_prev = 0.f, dpar = 0.f;
+        // learned-stop inputs before the merge (only on iterations whose
+        // features are used: traced, or where a stop may be taken)
+        float d1_prev = 0.f, dk_prev = 0.f;
         const int kk_prev = min(a.k, np);
-        if (learn) {
+        const bool evalz = a.mlp != nullptr && t + 1 >= a.t_min && (t + 1 - a.t_min) % a.t_every == 0;
+        const bool feats = learn && (a.trace_feat != nullptr || evalz);
+        if (feats) {
             d1_prev = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
             dk_prev = pool_dist<LW>(pool, kk_prev - 1, a.out_dtype, a.trav.metric);
-            uint32_t pv = key_to_out((uint32_t)(pkey >> 32), a.out_dtype, a.trav.metric);
-            dpar = a.out_dtype == SVF_U8 ? (float)(int32_t)pv : __uint_as_float(pv);
         }
 
         // only candidates below the pool's current L-th key can enter
@@ -273,10 +294,13 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
 #pragma unroll
             for (int s = 0; s < LW; s++) {
                 admitted += __popc(__ballot_sync(kFull, ((uint32_t)pool[s] & kNewBit) != 0 && !key_is_pad(pool[s])));
-                unexp += __popc(__ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0));
                 pool[s] &= ~(uint64_t)kNewBit;
             }
             if (newtop > 0) fs.t_last = t;
+            fs.ema = 0.5f * fs.ema + 0.5f * ((float)admitted / R);
+            if (!feats) continue;
+#pragma unroll
+            for (int s = 0; s < LW; s++) unexp += __popc(__ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0));
             float d1 = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
             float dk = pool_dist<LW>(pool, kk - 1, a.out_dtype, a.trav.metric);
             float dl = pool_dist<LW>(pool, np - 1, a.out_dtype, a.trav.metric);
@@ -288,28 +312,39 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
             float sum = mine;
 #pragma unroll
             for (int m = 16; m > 0; m >>= 1) sum += __shfl_xor_sync(kFull, sum, m);
-            const float mean = sum / kk;
+            const float inv_kk = kk == a.k ? inv_k : 1.f / (float)kk;
+            const float mean = sum * inv_kk;
             float dev = lane < kk ? (mine - mean) * (mine - mean) : 0.f;
 #pragma unroll
             for (int m = 16; m > 0; m >>= 1) dev += __shfl_xor_sync(kFull, dev, m);
-            const float inv = 1.f / fs.s0;
+            const float inv = inv_s0;
             float f[16];
-            f[0] = (float)(t + 1) / a.T;
+            f[0] = (float)(t + 1) * inv_T;
             f[1] = (fs.d1_0 - d1) * inv;
             f[2] = (dk - d1) * inv;
             f[3] = (dl - d1) * inv;
             f[4] = (mean - d1) * inv;
-            f[5] = sqrtf(dev / kk) * inv;
+            f[5] = sqrtf(dev * inv_kk) * inv;
             f[6] = (float)admitted / R;
             f[7] = (float)unexp / L;
-            f[8] = (float)newtop / a.k;
-            f[9] = (float)(t - fs.t_last) / a.T;
+            f[8] = (float)newtop * inv_k;
+            f[9] = (float)(t - fs.t_last) * inv_T;
             f[10] = (float)(np - unexp) / L;
             f[11] = (float)(ps * 32 + pl) / L;
             f[12] = (dk_prev - dk) * inv;
             f[13] = (d1_prev - d1) * inv;
-            f[14] = (dpar - d1) * inv;
-            fs.ema = 0.5f * fs.ema + 0.5f * f[6];
+            // the next parent: nearest unexpanded entry after the merge
+            int ns = -1, nl = 0;
+#pragma unroll
+            for (int s = 0; s < LW; s++) {
+                const uint32_t b = __ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0);
+                if (ns < 0 && b) {
+                    ns = s;
+                    nl = __ffs(b) - 1;
+                }
+            }
+            const float dnext = ns >= 0 ? pool_dist<LW>(pool, ns * 32 + nl, a.out_dtype, a.trav.metric) : dl;
+            f[14] = (dnext - dk) * inv;
             f[15] = fs.ema;
             if (a.trace_feat && lane < 16) {
                 float fv = f[0];
@@ -318,21 +353,22 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
                     if (lane == i) fv = f[i];
                 a.trace_feat[(qi * a.T + t) * 16 + lane] = fv;
             }
-            if (a.mlp && t + 1 >= a.t_min) {
-                // lane j computes hidden units j and j+32
-                const __nv_bfloat16 *wp = reinterpret_cast<const __nv_bfloat16 *>(a.mlp);
+            if (evalz) {
+                // lane j computes hidden units j and j+32 from its registers
                 float z = 0.f;
 #pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    const int j = lane + 32 * half;
-                    float h = __bfloat162float(wp[kMlpOffB1 + j]);
+                for (int h = 0; h < 2; h++) {
+                    float acc = __uint_as_float(hb[h] << 16);
 #pragma unroll
-                    for (int i = 0; i < 16; i++) h = fmaf(__bfloat162float(wp[j * 16 + i]), f[i], h);
-                    if (h > 0.f) z = fmaf(__bfloat162float(wp[kMlpOffW2 + j]), h, z);
+                    for (int i = 0; i < 8; i++) {
+                        acc = fmaf(__uint_as_float(w1p[h][i] << 16), f[2 * i], acc);
+                        acc = fmaf(__uint_as_float(w1p[h][i] & 0xFFFF0000u), f[2 * i + 1], acc);
+                    }
+                    if (acc > 0.f) z = fmaf(__uint_as_float(hb[h] & 0xFFFF0000u), acc, z);
                 }
 #pragma unroll
                 for (int m = 16; m > 0; m >>= 1) z += __shfl_xor_sync(kFull, z, m);
-                z += __bfloat162float(wp[kMlpOffB2]);
+                z += b2;
                 if (z >= a.z_tau) break;
             }
         }

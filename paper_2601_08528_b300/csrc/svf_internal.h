@@ -33,6 +33,7 @@ struct SearchArgs {
     const void *mlp;
     float z_tau;
     int t_min;
+    int t_every;
     float *trace_feat;
     int32_t *trace_meta;
     unsigned long long *status;

@@ -36,6 +36,7 @@ class SearchConfig:
     mlp: torch.Tensor | None = None  # packed bf16 stop network (device)
     tau: float = 0.5
     t_min: int = 4
+    t_every: int = 1
 
 
 class Index:
@@ -140,7 +141,8 @@ class Index:
         import math
         z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
         sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
-                            cfg.hash_log2, _ptr(qkeys), cfg.seed, _ptr(trace_feat), _ptr(trace_meta), _ptr(pool_out))
+                            cfg.hash_log2, _ptr(qkeys), cfg.seed, _ptr(trace_feat), _ptr(trace_meta), _ptr(pool_out),
+                            cfg.t_every, 0)
         L.check(L.load().svf_search(self._h, _ptr(Q), nq, C.byref(sp), _ptr(out_ids), _ptr(out_dist),
                                     _stream(stream)))
         return out_ids, out_dist

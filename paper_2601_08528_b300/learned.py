@@ -29,6 +29,7 @@ class StopNet:
     packed: torch.Tensor   # bf16 [1160] as int16 (what the search reads)
     tau: float = 0.5
     t_min: int = 4
+    t_every: int = 1
     loss: float = float("nan")
 
 
@@ -105,7 +106,8 @@ def calibrate(ix: Index, net: StopNet, Q: torch.Tensor, gt: torch.Tensor, cfg: S
     base_ids, _ = ix.search(Q, dataclasses.replace(cfg, mlp=None))
     r0 = recall_at_k(base_ids, gt)
     for tau in taus:
-        ids, _ = ix.search(Q, dataclasses.replace(cfg, mlp=net.packed, tau=tau, t_min=net.t_min))
+        ids, _ = ix.search(Q, dataclasses.replace(cfg, mlp=net.packed, tau=tau, t_min=net.t_min,
+                                                  t_every=net.t_every))
         r = recall_at_k(ids, gt)
         if r >= r0 - max_loss:
             return tau, r0, r

@@ -190,7 +190,8 @@ def test_adam_step_and_pack(svf, orc):
     assert (codes[1153:] == 0).all()
 
 
-def test_stop_decisions_match_oracle(svf, orc):
+@pytest.mark.parametrize("t_every", [1, 3])
+def test_stop_decisions_match_oracle(svf, orc, t_every):
     X, st, g = setup(orc, "u8", 4000, 64, "l2", 621)
     Q = synth.sample("u8", 200, 651)
     ix = make_index(svf, X, g, "l2", 64)
@@ -204,14 +205,15 @@ def test_stop_decisions_match_oracle(svf, orc):
     net = orc.MLP(prm[:1024].reshape(64, 16), prm[1024:1088], prm[1088:1152], float(prm[1152])).rounded_bf16()
     tau, T = 0.6, 64
     ids, dist = ix.search(torch.from_numpy(Q).cuda(),
-                          svf.SearchConfig(k=10, L=64, T=T, seed=8, mlp=packed, tau=tau, t_min=4))
-    o = orc.search_ex(st, 4000, g, None, Q, 10, 64, T, 8, net=net, tau=tau, t_min=4)
+                          svf.SearchConfig(k=10, L=64, T=T, seed=8, mlp=packed, tau=tau, t_min=4, t_every=t_every))
+    o = orc.search_ex(st, 4000, g, None, Q, 10, 64, T, 8, net=net, tau=tau, t_min=4, t_every=t_every)
     gi = P.as_u32(ids.cpu().numpy())
     same = (gi == o["ids"]).all(1)
     near = o["margin"] <= 1e-3  # the FP32 logit met the threshold within rounding
     assert not (~same & ~near).any(), f"{(~same & ~near).sum()} queries differ away from the threshold"
     stopped = o["stop_iter"] > 0
     assert stopped.mean() > 0.3 and same.mean() > 0.9
+    assert ((o["stop_iter"][stopped] - 4) % t_every == 0).all()
 
 
 def test_learned_stop_saves_iterations(svf, orc):

@@ -253,7 +253,7 @@ def test_search_init_is_the_draw_sequence(orc):
     base = orc.splitmix64(7 ^ orc.splitmix64(key))
     draws = []
     for j in range(4 * L):
-        i = orc.splitmix64(base ^ j) % n
+        i = ((orc.splitmix64(base ^ j) >> 32) * n) >> 32
         if i not in draws:
             draws.append(i)
         if len(draws) == L:
@@ -452,6 +452,18 @@ def test_stop_extremes_reduce_to_fixed_T(orc):
     r = orc.search_ex(st, n, g, None, Q, 10, 64, 32, 1, net=always, tau=0.5, t_min=6)
     np.testing.assert_array_equal(r["ids"], short["ids"])
     assert np.all(r["stop_iter"] == 6)
+    # evaluated every 4 iterations from t_min = 5: first chance after 5
+    r = orc.search_ex(st, n, g, None, Q, 10, 64, 32, 1, net=always, tau=0.5, t_min=5, t_every=4)
+    assert np.all(r["stop_iter"] == 5)
+    # a network that says "stop" only from t+1 >= 7 (b2 + 10 f0 with T=10),
+    # evaluated at 4, 7, 10: stops at 7
+    W1 = np.zeros((64, 16))
+    W1[0, 0] = 10.0
+    w2 = np.zeros(64)
+    w2[0] = 1.0
+    ramp = orc.MLP(W1, np.zeros(64), w2, -6.5)
+    r = orc.search_ex(st, n, g, None, Q, 10, 64, 10, 1, net=ramp, tau=0.5, t_min=4, t_every=3)
+    assert np.all(r["stop_iter"] == 7)
 
 
 def test_trace_features_and_labels(orc):
