@@ -70,12 +70,20 @@ def build_index(svf, torch, X, log_t):
     ix.build(torch.from_numpy(X[:n0]).cuda())
     torch.cuda.synchronize()
     log_t("bootstrap build", n0, time.time() - t)
-    t = time.time()
+    # inserts: host->device copy of each batch outside the timed region
+    ins_s = 0.0
     while ix.n_used < n:
         b = min(ix.n_used, MAX_BATCH, n - ix.n_used)
-        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=64, T_ins=48)
-    torch.cuda.synchronize()
-    log_t("inserts", n - n0, time.time() - t)
+        xb = torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.insert(xb, L_ins=64, T_ins=48)
+        e1.record()
+        e1.synchronize()
+        ins_s += e0.elapsed_time(e1) / 1e3
+    log_t("inserts", n - n0, ins_s)
+    ix.insert_rate = (n - n0) / ins_s if ins_s > 0 else None
     return ix
 
 
@@ -181,6 +189,31 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def csrc_hash():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2601_08528_b300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(form, L, T):
+    """DRAM bytes per launch from the committed ncu summary of the timed
+    configuration, if the kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "search_kernel_unit96_10M.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = dict(line.split(": ", 1) for line in txt.splitlines() if line.startswith(("traffic_bytes", "source_sha")))
+    head = txt.splitlines()[0]
+    if vals.get("source_sha", "").strip() != csrc_hash() or f"L={L}, T={T}" not in head or form.split("+")[0] not in head:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -357,7 +390,8 @@ def main():
         "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "L": v["L"], "T": v["T"], "iters": v["iters"]}
                   for k, v in best.items()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(form, cfg.L, cfg.T),
+                     "peak_source": src,
                      "alg_bytes_per_launch": alg, "iters_per_launch": iters, "evals_per_launch": evals,
                      "hash_resets": s["hash_resets"]},
         "e2e": {"value": world * nq * a.steps / e2e_t, "unit": "queries/s",
@@ -365,6 +399,16 @@ def main():
         "gpu_launches": a.steps,
         "clocks": clk,
     }
+    # deletes (1% of the index, uniformly drawn live ids) with localized repair
+    dels = torch.from_numpy(synth.pick_live_ids(a.n, None, a.n // 100, 304).view(np.int32)).cuda()
+    torch.cuda.synchronize()
+    t_del = time.time()
+    ix.delete(dels)
+    torch.cuda.synchronize()
+    t_del = time.time() - t_del
+    out["updates"] = {"inserts_per_s": ix.insert_rate, "insert_batch": MAX_BATCH, "L_ins": 64, "T_ins": 48,
+                      "deletes_per_s": dels.numel() / t_del, "delete_batch": dels.numel(),
+                      "repaired_rows": ix.stats()["repaired_rows"]}
     if rank == 0:
         # oracle timed on host cores: fixed-T FP64 search at the fp32 operating point
         fp = best.get("fp32", {"L": 256, "T": 192})
