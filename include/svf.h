@@ -150,6 +150,10 @@ typedef struct {
     uint64_t hash_resets;       /* visited-table resets */
     uint64_t repaired_rows;     /* rows rewritten by localized repair */
     uint64_t reverse_targets;   /* rows whose tail took reverse edges */
+    uint64_t cache_hits;        /* tiered store: rows read from the device cache */
+    uint64_t cache_misses;      /* tiered store: rows read from host memory */
+    uint64_t promoted;          /* tiered store: rows promoted into the cache */
+    uint64_t evicted;           /* tiered store: cached rows evicted */
 } svf_counters;
 
 typedef struct svf_index svf_index;
@@ -220,6 +224,103 @@ int svf_encode_fp8(const float *X, int64_t n, int32_t d, void *out, int64_t pitc
  * [nq][k] (int32 for U8, float otherwise; may be NULL). */
 int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, const void *Q, int64_t nq,
             const int64_t *self, int32_t k, uint64_t *work_keys, uint32_t *out_ids, void *out_dist, void *stream);
+
+/* ---- tiered store (serving form, Sec. 4.2-4.3, Alg. 2).
+ * After svf_tier_enable the primary (fp32/uint8) rows live in caller-pinned
+ * host memory and a device cache of M rows holds the hot ones; every kernel
+ * reads a row from its cache slot when mapped and from host memory (mapped,
+ * zero-copy) otherwise, so results do not depend on what is cached.  A miss
+ * adds to F_recent(x); x is queued for promotion when
+ *   F_lambda(x) = alpha * F_recent(x) + beta * log(1 + E_in(x)) > theta
+ * (Eq. 2, the threshold form of Eq. 1).  svf_tier_maintain promotes queued
+ * rows (highest F_lambda first) into victims chosen by a clock sweep over
+ * the cache that skips (and clears) referenced slots and takes the lowest
+ * F_lambda among unreferenced ones (Alg. 2), halves F_recent every
+ * decay_every misses, and adapts theta to the miss rate (Sec. 4.4).  It must
+ * not run while a search or update on the index is in flight.
+ * Enable warms the cache with the highest in-degree rows (cold start).  The
+ * device copy of the primary store is not read afterwards. */
+typedef struct {
+    int64_t M;              /* cache slots */
+    uint32_t qcap;          /* promotion queue capacity (<= 16384) */
+    int32_t promote_batch;  /* rows promoted per maintenance (<= 2048) */
+    int32_t sweep;          /* clock slots examined per promotion (sweep * batch <= 8192) */
+    float alpha, beta;      /* Eq. 2 weights (paper: alpha/(alpha+beta) ~ 0.6) */
+    float theta0;           /* initial promotion threshold */
+    uint64_t decay_every;   /* halve F_recent after this many misses */
+} svf_tier_params;
+
+typedef struct {
+    size_t cache, map, owner, ref, freq, ein, queue, scratch; /* device bytes */
+    size_t host;                                              /* pinned host bytes */
+} svf_tier_sizes;
+
+typedef struct {
+    void *cache; int32_t *map; int32_t *owner; uint8_t *ref; uint32_t *freq; uint32_t *ein; uint32_t *queue;
+    void *scratch;
+    void *host;  /* pinned (cudaHostAlloc / page-locked) host memory for n_cap rows */
+} svf_tier_buffers;
+
+int svf_tier_buffer_sizes(const svf_params *p, const svf_tier_params *tp, svf_tier_sizes *out);
+/* Copies rows [0, n_used) to the host store, computes E_in, warms the cache. */
+int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buffers *tb, void *stream);
+/* One maintenance round; *out_promoted (host, optional) = rows promoted. */
+int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream);
+/* Current promotion threshold. */
+float svf_tier_theta(svf_index *h);
+
+/* ---- continuous-batching request loop (Sec. 4.4 real-time coordination,
+ * Sec. 5.3 consistency).  A worker thread admits requests in submission
+ * order, each no earlier than its t_arrival (svf_serve_now clock; 0 = now).
+ * Searches run on n_streams streams with up to max_inflight batches on the
+ * GPU at once; an insert or delete waits for the in-flight searches, runs
+ * alone and advances the epoch, so each search reads exactly the state of
+ * its epoch (its result equals the same search run alone on that state).
+ * With a tiered store, svf_tier_maintain runs every maintain_every search
+ * batches while nothing is in flight.  All request buffers are device
+ * memory owned by the caller and must stay valid until the completion for
+ * the request has been polled. */
+enum svf_op { SVF_OP_SEARCH = 0, SVF_OP_INSERT = 1, SVF_OP_DELETE = 2 };
+
+typedef struct {
+    int32_t max_inflight;
+    int32_t n_streams;
+    int32_t maintain_every;
+    int32_t reserved0;
+} svf_serve_cfg;
+
+typedef struct {
+    int32_t op;               /* svf_op */
+    int32_t count;            /* queries / vectors / ids */
+    const void *data;         /* device: queries, vectors or uint32 ids */
+    svf_search_params sp;     /* search */
+    uint32_t *out_ids;        /* search: device [count][k] */
+    void *out_dist;           /* search: device [count][k] */
+    uint32_t *out_new_ids;    /* insert: device [count] (optional) */
+    int32_t L_ins, T_ins;     /* insert */
+    uint64_t tag;             /* caller's request id */
+    double t_arrival;         /* arrival time, svf_serve_now() clock */
+} svf_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t op;
+    int32_t status;           /* SVF_OK or an error code */
+    uint64_t epoch;           /* updates applied before (search) / after (update) it */
+    int64_t count;
+    double t_arrival, t_start, t_done;
+} svf_completion;
+
+typedef struct svf_server svf_server;
+
+double svf_serve_now(void);
+int svf_serve_start(svf_index *h, const svf_serve_cfg *cfg, svf_server **out);
+int svf_serve_submit(svf_server *s, const svf_request *r);
+int svf_serve_poll(svf_server *s, svf_completion *out, int max, int *n_out);
+/* Wait until every submitted request completed (SVF_ETIMEOUT after timeout_s);
+ * returns the first request error seen, if any. */
+int svf_serve_drain(svf_server *s, double timeout_s);
+int svf_serve_stop(svf_server *s);
 
 /* ---- allocation-free variant of svf_knn (the paper has no counterpart).
  * For callers that cannot call cudaMalloc -- a plugin or custom call inside

@@ -74,6 +74,7 @@ def lib():
             "orc_search_ex": (None, [S, I64, P, I32, P, P, I64, P, I32, I32, I32, U64, P, P, P, P, P, P,
                                      P, P, P, D, D, I32, I32, P, P]),
             "orc_dist_ids": (None, [S, P, I64, P, I32, P]),
+            "orc_wavp_round": (None, [I64, P, P, P, P, P, P, I64, I64, I64, I64, D, D, P, P]),
         }
         for name, (res, args) in sig.items():
             if not hasattr(_lib, name):
@@ -353,6 +354,16 @@ def search_ex(store: Store, n_used: int, graph: np.ndarray, delbits, Q: np.ndarr
                         _p(out["ids"]), _p(out["dist"]), _p(out["gap"]), _p(out.get("feat")), _p(out["n_feat"]),
                         _p(out["t_last"]), *args, z_tau, t_min, t_every, _p(out["stop_iter"]), _p(out["margin"]))
     return out
+
+
+def wavp_round(map_, owner, ref, freq, ein, queue, B, hand, W, alpha, beta):
+    """One batched round of Alg. 2 (in place on map_, owner, ref)."""
+    M = owner.shape[0]
+    p, e = np.zeros(1, np.int64), np.zeros(1, np.int64)
+    q = np.ascontiguousarray(queue, dtype=np.uint32)
+    lib().orc_wavp_round(M, _p(map_), _p(owner), _p(ref), _p(freq), _p(ein), _p(q), len(q), B, hand, W, alpha, beta,
+                         _p(p), _p(e))
+    return int(p[0]), int(e[0])
 
 
 def threads() -> int:

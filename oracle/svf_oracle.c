@@ -1163,3 +1163,77 @@ double orc_mlp_backward(const double *W1, const double *b1, const double *w2, do
     }
     return loss / (double)nb;
 }
+
+/* ------------------------------------------------------------------ */
+/* One maintenance round of workload-aware vector placement (Sec. 4.3,
+   Eq. 2, Alg. 2), batched: F(x) = alpha*freq(x) + beta*log(1 + ein(x)).
+   Candidates: queue[0..c) ordered by descending F (ties: ascending id), the
+   first B.  Victims: the W slots from the clock hand (mod M); a referenced
+   slot loses its bit and is passed over (second chance); the unreferenced
+   ones are ordered by ascending F of their owner (an empty slot first,
+   ties: ascending slot); if fewer than B were unreferenced the clock comes
+   round the window again, when every slot in it is unreferenced (Alg. 2's
+   sweep continues until it finds a victim).  The i-th candidate replaces the i-th victim for
+   i < min(B, #victims): the evicted owner's map entry becomes -1, the
+   candidate maps to the slot, and the slot's reference bit is set. */
+typedef struct {
+    double f;
+    int64_t k;
+} fk;
+static int fk_desc(const void *pa, const void *pb) {
+    const fk *a = (const fk *)pa, *b = (const fk *)pb;
+    if (a->f != b->f) return a->f > b->f ? -1 : 1;
+    return (a->k > b->k) - (a->k < b->k);
+}
+static int fk_asc(const void *pa, const void *pb) {
+    const fk *a = (const fk *)pa, *b = (const fk *)pb;
+    if (a->f != b->f) return a->f < b->f ? -1 : 1;
+    return (a->k > b->k) - (a->k < b->k);
+}
+void orc_wavp_round(int64_t M, int32_t *map, int32_t *owner, uint8_t *ref, const uint32_t *freq, const uint32_t *ein,
+                    const uint32_t *queue, int64_t c, int64_t B, int64_t hand, int64_t W, double alpha, double beta,
+                    int64_t *promoted, int64_t *evicted) {
+    fk *cand = (fk *)malloc(sizeof(fk) * (size_t)(c > 0 ? c : 1));
+    fk *vic = (fk *)malloc(sizeof(fk) * (size_t)(W > 0 ? W : 1));
+    for (int64_t i = 0; i < c; i++) {
+        uint32_t x = queue[i];
+        cand[i].f = alpha * freq[x] + beta * log(1.0 + ein[x]);
+        cand[i].k = x;
+    }
+    qsort(cand, (size_t)c, sizeof(fk), fk_desc);
+    int64_t nv = 0;
+    int64_t want = B < c ? B : c;
+    for (int pass = 0; pass < 2 && (pass == 0 || nv < want); pass++) {
+        nv = 0;
+        for (int64_t i = 0; i < W; i++) {
+            int64_t s = (hand + i) % M;
+            if (ref[s]) {
+                ref[s] = 0;
+                continue;
+            }
+            int32_t o = owner[s];
+            vic[nv].f = o < 0 ? -INFINITY : alpha * freq[o] + beta * log(1.0 + ein[o]);
+            vic[nv].k = s;
+            nv++;
+        }
+    }
+    qsort(vic, (size_t)nv, sizeof(fk), fk_asc);
+    int64_t np = B < c ? B : c;
+    if (nv < np) np = nv;
+    *promoted = 0;
+    *evicted = 0;
+    for (int64_t i = 0; i < np; i++) {
+        int64_t s = vic[i].k;
+        uint32_t x = (uint32_t)cand[i].k;
+        if (owner[s] >= 0) {
+            map[owner[s]] = -1;
+            (*evicted)++;
+        }
+        owner[s] = (int32_t)x;
+        map[x] = (int32_t)s;
+        ref[s] = 1;
+        (*promoted)++;
+    }
+    free(cand);
+    free(vic);
+}

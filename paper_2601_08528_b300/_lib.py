@@ -23,7 +23,9 @@ MLP_PARAMS, MLP_PACKED = 1153, 1160
 SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "svf_attach", "svf_build", "svf_search",
            "svf_insert", "svf_delete", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
            "svf_encode_fp8", "svf_knn", "svf_mlp_grad", "svf_mlp_partial_floats", "svf_mlp_adam", "svf_mlp_pack",
-           "svf_mlp_forward"]
+           "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta",
+           "svf_serve_now", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
+           "svf_serve_stop"]
 
 
 class Params(C.Structure):
@@ -54,7 +56,40 @@ class SearchParams(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("n_used", C.c_int64), ("n_deleted", C.c_int64), ("search_queries", C.c_uint64),
                 ("search_iters", C.c_uint64), ("search_evals", C.c_uint64), ("hash_resets", C.c_uint64),
-                ("repaired_rows", C.c_uint64), ("reverse_targets", C.c_uint64)]
+                ("repaired_rows", C.c_uint64), ("reverse_targets", C.c_uint64), ("cache_hits", C.c_uint64),
+                ("cache_misses", C.c_uint64), ("promoted", C.c_uint64), ("evicted", C.c_uint64)]
+
+
+class TierParams(C.Structure):
+    _fields_ = [("M", C.c_int64), ("qcap", C.c_uint32), ("promote_batch", C.c_int32), ("sweep", C.c_int32),
+                ("alpha", C.c_float), ("beta", C.c_float), ("theta0", C.c_float), ("decay_every", C.c_uint64)]
+
+
+class TierSizes(C.Structure):
+    _fields_ = [(f, C.c_size_t) for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch", "host")]
+
+
+class TierBuffers(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch", "host")]
+
+
+OP_SEARCH, OP_INSERT, OP_DELETE = 0, 1, 2
+
+
+class ServeCfg(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("n_streams", C.c_int32), ("maintain_every", C.c_int32),
+                ("reserved0", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("op", C.c_int32), ("count", C.c_int32), ("data", C.c_void_p), ("sp", SearchParams),
+                ("out_ids", C.c_void_p), ("out_dist", C.c_void_p), ("out_new_ids", C.c_void_p), ("L_ins", C.c_int32),
+                ("T_ins", C.c_int32), ("tag", C.c_uint64), ("t_arrival", C.c_double)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("op", C.c_int32), ("status", C.c_int32), ("epoch", C.c_uint64),
+                ("count", C.c_int64), ("t_arrival", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
 
 
 class SvfError(RuntimeError):
@@ -96,6 +131,16 @@ def load() -> C.CDLL:
         "svf_mlp_adam": (I32, [P, P, P, P, I64, C.c_float, C.c_float, C.c_float, C.c_float, P]),
         "svf_mlp_pack": (I32, [P, P, P]),
         "svf_mlp_forward": (I32, [P, P, I64, P, P]),
+        "svf_tier_buffer_sizes": (I32, [C.POINTER(Params), C.POINTER(TierParams), C.POINTER(TierSizes)]),
+        "svf_tier_enable": (I32, [P, C.POINTER(TierParams), C.POINTER(TierBuffers), P]),
+        "svf_tier_maintain": (I32, [P, C.POINTER(C.c_int64), P]),
+        "svf_tier_theta": (C.c_float, [P]),
+        "svf_serve_now": (C.c_double, []),
+        "svf_serve_start": (I32, [P, C.POINTER(ServeCfg), C.POINTER(C.c_void_p)]),
+        "svf_serve_submit": (I32, [P, C.POINTER(Request)]),
+        "svf_serve_poll": (I32, [P, C.POINTER(Completion), I32, C.POINTER(C.c_int32)]),
+        "svf_serve_drain": (I32, [P, C.c_double]),
+        "svf_serve_stop": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

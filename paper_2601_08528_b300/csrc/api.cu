@@ -7,16 +7,16 @@
 #include <cstring>
 #include <string>
 
-#include "svf_internal.h"
+#include "index_impl.h"
 #include "svf_mlp.h"
-#include "svf_update.h"
 
 using namespace svf;
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
 
-int fail(int code, const char *fmt, ...) {
+int svf::fail(int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -26,30 +26,7 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-#define CUDA_TRY(expr)                                                                              \
-    do {                                                                                            \
-        cudaError_t e_ = (expr);                                                                    \
-        if (e_ != cudaSuccess) return fail(SVF_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));     \
-    } while (0)
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-int esize_of(int dtype) { return dtype == SVF_U8 ? 1 : 4; }
-int64_t fp8_pitch(int d) { return ((int64_t)d + 4 + 31) / 32 * 32; }
-
-struct WsLayout {
-    size_t head, vl, newrows, region, total;
-    // region views
-    size_t knn_keys, knn_ids;                       // build
-    size_t pool, rows, dkeys, next;                 // insert
-    size_t cand;                                    // delete
-    int64_t max_batch;
-};
-
-constexpr int kInsertLmax = 256;
-constexpr int64_t kDeleteChunk = 16384;
-
-WsLayout ws_layout(const svf_params &p, int64_t max_batch) {
+WsLayout svf::ws_layout(const svf_params &p, int64_t max_batch) {
     WsLayout w{};
     const int64_t R = p.R, n = p.n_cap;
     size_t off = 0;
@@ -86,15 +63,7 @@ WsLayout ws_layout(const svf_params &p, int64_t max_batch) {
     return w;
 }
 
-// Lanes per row when distances are computed from staged rows: the smallest
-// power of two that leaves at most 4 chunks of 16 bytes per lane.
-void set_team(RowDesc &r) {
-    int ts = 1;
-    while (ts < 32 && (r.nchunk + ts - 1) / ts > 4) ts <<= 1;
-    r.ts = ts;
-    r.cpl = (r.nchunk + ts - 1) / ts;
-}
-
+namespace {
 int check_params(const svf_params *p) {
     if (!p) return fail(SVF_EINVAL, "null params");
     if (p->d < 16 || p->d > 2048 || p->d % 16) return fail(SVF_EINVAL, "d=%d: need 16..2048, multiple of 16", p->d);
@@ -110,49 +79,6 @@ int check_params(const svf_params *p) {
     return SVF_OK;
 }
 }  // namespace
-
-struct svf_index {
-    svf_params p;
-    svf_buffers b;
-    WsLayout ws;
-    int64_t n_used = 0;
-    uint64_t repaired = 0;
-    cudaStream_t last = nullptr;
-    unsigned long long *status() const { return reinterpret_cast<unsigned long long *>(b.status); }
-    uint8_t *wsp(size_t off) const { return reinterpret_cast<uint8_t *>(b.workspace) + off; }
-    RowDesc prim() const {
-        RowDesc r{};
-        r.base = reinterpret_cast<const uint8_t *>(b.vecs);
-        r.pitch = (int64_t)p.d * esize_of(p.dtype);
-        r.nchunk = (int)(r.pitch / 16);
-        r.d = p.d;
-        r.dtype = p.dtype;
-        r.metric = p.metric;
-        r.copy_bytes = (int)r.pitch;
-        set_team(r);
-        return r;
-    }
-    RowDesc lowp(int which) const {
-        RowDesc r{};
-        r.d = p.d;
-        r.metric = p.metric;
-        if (which == SVF_BF16) {
-            r.base = reinterpret_cast<const uint8_t *>(b.vecs_bf16);
-            r.pitch = (int64_t)p.d * 2;
-            r.nchunk = p.d / 8;
-            r.dtype = SVF_BF16;
-            r.copy_bytes = 2 * p.d;
-        } else {
-            r.base = reinterpret_cast<const uint8_t *>(b.vecs_fp8);
-            r.pitch = fp8_pitch(p.d);
-            r.nchunk = p.d / 16;
-            r.dtype = SVF_FP8;
-            r.copy_bytes = (p.d + 4 + 15) / 16 * 16;
-        }
-        set_team(r);
-        return r;
-    }
-};
 
 extern "C" {
 
@@ -233,6 +159,7 @@ static int encode_lowp(svf_index *h, int64_t row0, int64_t m, cudaStream_t st) {
 
 int svf_build(svf_index *h, const void *X, int64_t n, void *stream) {
     if (!h || (!X && n > 0)) return fail(SVF_EINVAL, "null index / X");
+    if (h->tier.on) return fail(SVF_EINVAL, "build is not available once the store is tiered");
     if (n < 0 || n > h->p.n_cap) return fail(SVF_ECAPACITY, "n=%lld exceeds n_cap", (long long)n);
     if (n > h->ws.max_batch) return fail(SVF_EINVAL, "n=%lld exceeds the workspace's max_batch %lld", (long long)n,
                                          (long long)h->ws.max_batch);
@@ -306,6 +233,7 @@ static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search
     a.trace_feat = sp->trace_feat;
     a.trace_meta = sp->trace_meta;
     a.status = h->status();
+    a.tier = h->tier_ctx();
     CUDA_TRY(launch_search(a, h->p.R, sp->L, st));
     return SVF_OK;
 }
@@ -352,9 +280,12 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     const RowDesc P = h->prim();
     const int64_t n0 = h->n_used;
     const int R = h->p.R;
-    CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<uint8_t *>(h->b.vecs) + n0 * P.pitch, X, (size_t)m * P.pitch,
-                             cudaMemcpyDeviceToDevice, st));
-    int rc = encode_lowp(h, n0, m, st);
+    // the new rows: into the primary store (device, or host rows of a tiered
+    // store, where they stay uncached until promoted)
+    uint8_t *dst = h->tier.on ? h->tier.host : reinterpret_cast<uint8_t *>(h->b.vecs);
+    CUDA_TRY(cudaMemcpyAsync(dst + n0 * P.pitch, X, (size_t)m * P.pitch,
+                             h->tier.on ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    int rc = h->tier.on ? SVF_OK : encode_lowp(h, n0, m, st);
     if (rc) return rc;
     uint64_t *pool = reinterpret_cast<uint64_t *>(h->wsp(h->ws.region + h->ws.pool));
     uint32_t *rows = reinterpret_cast<uint32_t *>(h->wsp(h->ws.region + h->ws.rows));
@@ -368,7 +299,7 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     sp.T = T_ins;
     sp.precision = h->p.dtype;
     sp.pool_out = pool;
-    rc = search_impl(h, reinterpret_cast<uint8_t *>(h->b.vecs) + n0 * P.pitch, m, &sp, rows, dkeys, st, n0, P);
+    rc = search_impl(h, X, m, &sp, rows, dkeys, st, n0, P);
     if (rc) return rc;
     // 2. reorder each pool into the new row
     PruneArgs a{};
@@ -460,6 +391,10 @@ int svf_stats(svf_index *h, svf_counters *out) {
     out->hash_resets = s[kStResets];
     out->repaired_rows = h->repaired;
     out->reverse_targets = s[kStRevTargets];
+    out->cache_hits = s[kStHits];
+    out->cache_misses = s[kStMisses];
+    out->promoted = s[kStPromoted];
+    out->evicted = s[kStEvicted];
     return SVF_OK;
 }
 
@@ -469,6 +404,9 @@ int svf_stats_reset(svf_index *h) {
     unsigned long long s[kStWords];
     CUDA_TRY(cudaMemcpy(s, h->status(), sizeof s, cudaMemcpyDeviceToHost));
     for (int i = kStQueries; i <= kStRevTargets; i++) s[i] = 0;
+    for (int i = kStHits; i <= kStMisses; i++) s[i] = 0;
+    s[kStPromoted] = s[kStEvicted] = 0;
+    h->tier.last_hits = h->tier.last_misses = h->tier.misses_at_decay = 0;
     h->repaired = 0;
     CUDA_TRY(cudaMemcpy(h->status(), s, sizeof s, cudaMemcpyHostToDevice));
     return SVF_OK;

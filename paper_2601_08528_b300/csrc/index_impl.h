@@ -1,0 +1,130 @@
+// index_impl.h -- the host-side index object behind the C ABI (shared by
+// api.cu and tier.cu): parameters, borrowed buffers, workspace layout, and
+// the row descriptors of the stores.
+#pragma once
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "svf_internal.h"
+#include "svf_update.h"
+
+namespace svf {
+
+int fail(int code, const char *fmt, ...);
+
+#define CUDA_TRY(expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess) return svf::fail(SVF_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline int esize_of(int dtype) { return dtype == SVF_U8 ? 1 : 4; }
+inline int64_t fp8_pitch(int d) { return ((int64_t)d + 4 + 31) / 32 * 32; }
+
+// Lanes per row when distances are computed from staged rows: the smallest
+// power of two that leaves at most 4 chunks of 16 bytes per lane.
+inline void set_team(RowDesc &r) {
+    int ts = 1;
+    while (ts < 32 && (r.nchunk + ts - 1) / ts > 4) ts <<= 1;
+    r.ts = ts;
+    r.cpl = (r.nchunk + ts - 1) / ts;
+}
+
+struct WsLayout {
+    size_t head, vl, newrows, region, total;
+    size_t knn_keys, knn_ids;        // build
+    size_t pool, rows, dkeys, next;  // insert
+    size_t cand;                     // delete
+    int64_t max_batch;
+};
+
+constexpr int kInsertLmax = 256;
+constexpr int64_t kDeleteChunk = 16384;
+
+WsLayout ws_layout(const svf_params &p, int64_t max_batch);
+
+// Tiered store state (serving form): device cache + host rows + WAVP tables.
+struct Tier {
+    bool on = false;
+    uint8_t *host = nullptr;  // pinned host rows [n_cap][pitch]
+    uint8_t *cache = nullptr; // device cache [M][pitch]
+    int64_t M = 0;
+    int32_t *map = nullptr;   // [n_cap]
+    int32_t *owner = nullptr; // [M]
+    uint8_t *ref = nullptr;   // [M]
+    uint32_t *freq = nullptr; // [n_cap]
+    uint32_t *ein = nullptr;  // [n_cap]
+    uint32_t *queue = nullptr;
+    uint32_t qcap = 0;
+    uint64_t *scratch = nullptr;  // maintenance keys
+    float alpha = 0.6f, beta = 0.4f, theta = 2.0f, theta0 = 2.0f;
+    int promote_batch = 2048, sweep = 4;
+    uint64_t decay_every = 1 << 16;
+    int64_t clock = 0;
+    uint64_t last_hits = 0, last_misses = 0, misses_at_decay = 0, rounds = 0;
+    double last_rate = 0.0, last_meanf = 0.0;
+};
+
+}  // namespace svf
+
+struct svf_index {
+    svf_params p;
+    svf_buffers b;
+    svf::WsLayout ws;
+    int64_t n_used = 0;
+    uint64_t repaired = 0;
+    cudaStream_t last = nullptr;
+    svf::Tier tier;
+    unsigned long long *status() const { return reinterpret_cast<unsigned long long *>(b.status); }
+    uint8_t *wsp(size_t off) const { return reinterpret_cast<uint8_t *>(b.workspace) + off; }
+    svf::RowDesc prim() const {
+        svf::RowDesc r{};
+        r.pitch = (int64_t)p.d * svf::esize_of(p.dtype);
+        r.base = tier.on ? tier.cache : reinterpret_cast<const uint8_t *>(b.vecs);
+        r.map = tier.on ? tier.map : nullptr;
+        r.host = tier.on ? tier.host : nullptr;
+        r.nchunk = (int)(r.pitch / 16);
+        r.d = p.d;
+        r.dtype = p.dtype;
+        r.metric = p.metric;
+        r.copy_bytes = (int)r.pitch;
+        svf::set_team(r);
+        return r;
+    }
+    svf::RowDesc lowp(int which) const {
+        svf::RowDesc r{};
+        r.d = p.d;
+        r.metric = p.metric;
+        if (which == SVF_BF16) {
+            r.base = reinterpret_cast<const uint8_t *>(b.vecs_bf16);
+            r.pitch = (int64_t)p.d * 2;
+            r.nchunk = p.d / 8;
+            r.dtype = SVF_BF16;
+            r.copy_bytes = 2 * p.d;
+        } else {
+            r.base = reinterpret_cast<const uint8_t *>(b.vecs_fp8);
+            r.pitch = svf::fp8_pitch(p.d);
+            r.nchunk = p.d / 16;
+            r.dtype = SVF_FP8;
+            r.copy_bytes = (p.d + 4 + 15) / 16 * 16;
+        }
+        svf::set_team(r);
+        return r;
+    }
+    svf::TierCtx tier_ctx() const {
+        svf::TierCtx t{};
+        if (!tier.on) return t;
+        t.ref = tier.ref;
+        t.freq = tier.freq;
+        t.ein = tier.ein;
+        t.queue = tier.queue;
+        t.qcount = status() + svf::kStQCount;
+        t.qcap = tier.qcap;
+        t.alpha = tier.alpha;
+        t.beta = tier.beta;
+        t.theta = tier.theta;
+        return t;
+    }
+};

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(THREADS) prune_kernel(const PruneArgs a, int s
             if (stage) {
                 for (int e = tid; e < mm * nchunk; e += THREADS) {
                     int i = e / nchunk, c = e % nchunk;
-                    rows[e] = __ldg(reinterpret_cast<const uint4 *>(a.X.base + (int64_t)ids[i] * a.X.pitch) + c);
+                    rows[e] = reinterpret_cast<const uint4 *>(row_ptr(a.X, ids[i]))[c];
                 }
             }
             __syncthreads();
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(THREADS) prune_kernel(const PruneArgs a, int s
                     ri = rows + (size_t)i * nchunk;
                     rj = rows + (size_t)j * nchunk;
                 } else {
-                    ri = reinterpret_cast<const uint4 *>(a.X.base + (int64_t)ids[i] * a.X.pitch);
-                    rj = reinterpret_cast<const uint4 *>(a.X.base + (int64_t)ids[j] * a.X.pitch);
+                    ri = reinterpret_cast<const uint4 *>(row_ptr(a.X, ids[i]));
+                    rj = reinterpret_cast<const uint4 *>(row_ptr(a.X, ids[j]));
                 }
                 // invalid teams compute a harmless dummy pair (rows 0, 0)
                 uint32_t key = team_pair_key<DT>(a.X.metric, valid ? rj : ri, ri, valid ? nchunk : 0, sub);

@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
         __syncwarp();
     }
     int hcount = np;
-    if (!staged_dist<DT>(stg, a.trav, list, np, keys, 0u, lane, qf, qb)) {
+    const TierCtx *tier = a.trav.map ? &a.tier : nullptr;
+    int hits = 0, misses = 0;
+    if (!staged_dist<DT>(stg, a.trav, list, np, keys, 0u, lane, qf, qb, tier, &hits, &misses)) {
         if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
         return;
     }
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
         }
         evals += nf - ndel;
         const uint32_t newflag = learn ? kNewBit : 0u;
-        if (!staged_dist<DT>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb)) {
+        if (!staged_dist<DT>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb, tier, &hits, &misses)) {
             if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
             return;
         }
@@ -386,7 +388,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
         }
         __syncwarp();
         // the fp32 query is still in shared memory
-        if (!staged_dist<SVF_F32>(stg, a.prim, list, npool, keys, 0u, lane, qf, qb)) {
+        if (!staged_dist<SVF_F32>(stg, a.prim, list, npool, keys, 0u, lane, qf, qb, a.prim.map ? &a.tier : nullptr,
+                                  &hits, &misses)) {
             if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
             return;
         }
@@ -422,6 +425,10 @@ __global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchA
         atomicAdd(a.status + kStIters, (unsigned long long)iters);
         atomicAdd(a.status + kStEvals, (unsigned long long)evals);
         if (resets) atomicAdd(a.status + kStResets, (unsigned long long)resets);
+        if (tier) {
+            atomicAdd(a.status + kStHits, (unsigned long long)hits);
+            atomicAdd(a.status + kStMisses, (unsigned long long)misses);
+        }
     }
 }
 

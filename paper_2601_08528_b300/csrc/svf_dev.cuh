@@ -156,7 +156,20 @@ struct RowDesc {
     int copy_bytes;       // bytes staged per row (values, + the FP8 scale), multiple of 16
     int ts;               // lanes per row when staged (power of two, <= 32)
     int cpl;              // chunks per lane = ceil(nchunk / ts)
+    const int32_t *map;   // tiered store: device cache slot of each id (-1: host row), or null
+    const uint8_t *host;  // tiered store: all rows in mapped pinned host memory
 };
+
+// Address of row `id`: the store itself, or for a tiered store its device
+// cache slot when cached and its host row otherwise (host memory is read
+// through the mapping; the tier tables do not change while a kernel runs).
+__device__ __forceinline__ const uint8_t *row_ptr(const RowDesc &R, uint32_t id) {
+    if (R.map) {
+        const int32_t s = __ldg(R.map + id);
+        return s >= 0 ? R.base + (int64_t)s * R.pitch : R.host + (int64_t)id * R.pitch;
+    }
+    return R.base + (int64_t)id * R.pitch;
+}
 
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
     acc = fmaf(a.x, b.x, acc);
@@ -258,8 +271,8 @@ __device__ __forceinline__ void team_dist_key2(const RowDesc &R, uint32_t ida, b
                                                uint32_t &kb) {
     float fa = 0.0f, fb = 0.0f, sa = 1.0f, sb = 1.0f;
     uint32_t ia = 0, ib = 0;
-    const uint8_t *ra = R.base + (int64_t)ida * R.pitch;
-    const uint8_t *rb = R.base + (int64_t)idb * R.pitch;
+    const uint8_t *ra = row_ptr(R, ida);
+    const uint8_t *rb = row_ptr(R, idb);
     if (DT == SVF_FP8) {
         if (va) sa = __ldg(reinterpret_cast<const float *>(ra + R.d));
         if (vb) sb = __ldg(reinterpret_cast<const float *>(rb + R.d));
@@ -384,6 +397,11 @@ enum StatusWord {
     kStRepaired = 6,
     kStRevTargets = 7,
     kStNewlyDeleted = 8,
+    kStHits = 9,       // tiered store: distance rows read from the device cache
+    kStMisses = 10,    // tiered store: rows read from host memory
+    kStQCount = 11,    // tiered store: promotion candidates queued
+    kStPromoted = 12,  // tiered store: rows promoted into the cache
+    kStEvicted = 13,   // tiered store: cached rows evicted
     kStScratch0 = 16,  // per-call scratch counters
     kStWords = 64
 };
@@ -437,27 +455,90 @@ struct Stage {
     uint32_t phase;   // parity of the next phase to wait for
 };
 
+// Workload-aware placement state used on cache misses (SVFusion Sec. 4.3):
+// F_lambda(x) = alpha * F_recent(x) + beta * log(1 + E_in(x)); a missed x with
+// F_lambda > theta is queued for promotion (once: bit 31 of freq marks it).
+struct TierCtx {
+    uint8_t *ref;          // clock reference bit per cache slot
+    uint32_t *freq;        // F_recent per id (bit 31: queued)
+    const uint32_t *ein;   // E_in per id
+    uint32_t *queue;       // promotion candidates
+    unsigned long long *qcount;
+    uint32_t qcap;
+    float alpha, beta, theta;
+};
+constexpr uint32_t kQueuedBit = 0x80000000u;
+
+__device__ __forceinline__ void tier_miss(const TierCtx &T, uint32_t id) {
+    const uint32_t old = atomicAdd(T.freq + id, 1u);
+    if (old & kQueuedBit) return;
+    const float f = T.alpha * (float)((old & ~kQueuedBit) + 1u) + T.beta * log1pf((float)__ldg(T.ein + id));
+    if (f <= T.theta) return;
+    const uint32_t prev = atomicOr(T.freq + id, kQueuedBit);
+    if (prev & kQueuedBit) return;
+    const unsigned long long pos = atomicAdd(T.qcount, 1ull);
+    if (pos < T.qcap)
+        T.queue[pos] = id;
+    else
+        atomicAnd(T.freq + id, ~kQueuedBit);  // queue full: let a later miss queue it
+}
+
 // Distance keys of rows list[0..n) (smem ids) written to keys[0..n) with
 // `flags` or'ed into the id word.  Rows are staged in chunks that fit the
 // buffer; each chunk is one batch of bulk copies and one barrier wait.
 // Returns false if a wait gave up (the caller reports SVF_ETIMEOUT).
 template <int DT>
 __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const uint32_t *list, int n, uint64_t *keys,
-                                            uint32_t flags, int lane, const float *qf, const uint8_t *qb) {
+                                            uint32_t flags, int lane, const float *qf, const uint8_t *qb,
+                                            const TierCtx *tier = nullptr, int *hits = nullptr, int *misses = nullptr) {
     const int per = (int)(S.cap / (uint32_t)R.copy_bytes);
     const int ts = R.ts, team = lane / ts, sub = lane % ts, nteam = 32 / ts;
     for (int i0 = 0; i0 < n; i0 += per) {
         const int cnt = min(per, n - i0);
         __syncwarp();
         fence_proxy_async();  // earlier reads of the buffer precede the new async writes
-        if (lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(cnt * R.copy_bytes));
-        __syncwarp();
-        for (int j = lane; j < cnt; j += 32)
-            bulk_g2s(S.buf + (size_t)j * R.copy_bytes, R.base + (int64_t)list[i0 + j] * R.pitch, R.copy_bytes, S.mbar);
-        uint32_t it = 0;
-        while (!mbar_try_wait(S.mbar, S.phase))
-            if (++it > kWaitLimit) return false;
-        S.phase ^= 1u;
+        if (!R.map) {
+            if (lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(cnt * R.copy_bytes));
+            __syncwarp();
+            for (int j = lane; j < cnt; j += 32)
+                bulk_g2s(S.buf + (size_t)j * R.copy_bytes, R.base + (int64_t)list[i0 + j] * R.pitch, R.copy_bytes,
+                         S.mbar);
+            uint32_t it = 0;
+            while (!mbar_try_wait(S.mbar, S.phase))
+                if (++it > kWaitLimit) return false;
+            S.phase ^= 1u;
+        } else {
+            // tiered store: cached rows by bulk copy from the device cache,
+            // missed rows read from host memory by the lane that owns them
+            int nhit = 0;
+            for (int j = lane; j < cnt; j += 32) nhit += __ldg(R.map + list[i0 + j]) >= 0;
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) nhit += __shfl_xor_sync(kFull, nhit, m);
+            if (nhit > 0 && lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(nhit * R.copy_bytes));
+            __syncwarp();
+            for (int j = lane; j < cnt; j += 32) {
+                const uint32_t id = list[i0 + j];
+                const int32_t slot = __ldg(R.map + id);
+                uint8_t *dst = S.buf + (size_t)j * R.copy_bytes;
+                if (slot >= 0) {
+                    bulk_g2s(dst, R.base + (int64_t)slot * R.pitch, R.copy_bytes, S.mbar);
+                    tier->ref[slot] = 1;
+                } else {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(R.host + (int64_t)id * R.pitch);
+                    for (int c = 0; c < R.copy_bytes / 16; c++) reinterpret_cast<uint4 *>(dst)[c] = src[c];
+                    tier_miss(*tier, id);
+                }
+            }
+            if (hits) *hits += nhit;
+            if (misses) *misses += cnt - nhit;
+            if (nhit > 0) {
+                uint32_t it = 0;
+                while (!mbar_try_wait(S.mbar, S.phase))
+                    if (++it > kWaitLimit) return false;
+                S.phase ^= 1u;
+            }
+            __syncwarp();
+        }
         for (int r0 = 0; r0 < cnt; r0 += nteam) {
             const int r = r0 + team;
             const bool valid = r < cnt;

@@ -37,6 +37,7 @@ struct SearchArgs {
     float *trace_feat;
     int32_t *trace_meta;
     unsigned long long *status;
+    TierCtx tier;     // tiered store (used when trav.map is set)
     int list_len;
     uint32_t stage_bytes;
     size_t warp_smem;

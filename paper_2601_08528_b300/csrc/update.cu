@@ -40,12 +40,12 @@ __global__ void rev_merge_kernel(const RowDesc X, uint32_t *graph, int R, const 
     uint32_t t = lane < TL ? row[H + lane] : kEmpty;
     bool live = t != kEmpty && (int64_t)t < n0 && !is_deleted(del, t);
     uint64_t best[1] = {kPad};
-    const uint4 *ru = reinterpret_cast<const uint4 *>(X.base + (int64_t)u * X.pitch);
+    const uint4 *ru = reinterpret_cast<const uint4 *>(row_ptr(X, u));
     for (int b = 0; b < TL; b += 4) {
         const int e = b + team;  // entry evaluated by this team
         const uint32_t te = __shfl_sync(kFull, t, e & 31);
         const bool le = __shfl_sync(kFull, live, e & 31) && e < TL;
-        const uint4 *rt = reinterpret_cast<const uint4 *>(X.base + (int64_t)(le ? te : u) * X.pitch);
+        const uint4 *rt = reinterpret_cast<const uint4 *>(row_ptr(X, le ? te : u));
         const uint32_t key = team_pair_key<DT>(X.metric, ru, rt, le ? X.nchunk : 0, sub);
         const uint64_t full = le ? make_key(key, te) : kPad;
         // entry b+s is held by the lanes of team s; bring it to lane b+s
@@ -221,12 +221,12 @@ __global__ void del_gather_kernel(const RowDesc X, const uint32_t *graph, int R,
     }
     __syncwarp();
     // distances to u (teams of 8)
-    const uint4 *ru = reinterpret_cast<const uint4 *>(X.base + (int64_t)u * X.pitch);
+    const uint4 *ru = reinterpret_cast<const uint4 *>(row_ptr(X, u));
     for (int b0 = 0; b0 < n; b0 += 4) {
         const int e = b0 + team;
         const bool ve = e < n;
         const uint32_t w = ve ? list[e] : u;
-        const uint4 *rw = reinterpret_cast<const uint4 *>(X.base + (int64_t)w * X.pitch);
+        const uint4 *rw = reinterpret_cast<const uint4 *>(row_ptr(X, w));
         uint32_t key = team_pair_key<DT>(X.metric, ru, rw, ve ? X.nchunk : 0, sub);
         if (ve && sub == 0) dks[e] = key;
     }

@@ -160,6 +160,42 @@ class Index:
         L.check(L.load().svf_delete(self._h, _ptr(ids), ids.numel(), _ptr(newly), _stream(stream)))
         return int(newly.item())
 
+    # ------------------------------------------------------------ tiered store
+    def enable_tier(self, M: int, qcap: int = 16384, promote_batch: int = 2048, sweep: int = 4, alpha: float = 0.6,
+                    beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16) -> None:
+        """Move the primary rows to pinned host memory behind a device cache of
+        M rows with workload-aware placement (see svf_tier_enable)."""
+        lib = L.load()
+        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every)
+        sz = L.TierSizes()
+        L.check(lib.svf_tier_buffer_sizes(C.byref(self.params), C.byref(tp), C.byref(sz)))
+        u8 = torch.uint8
+        self.tier_bufs = {f: torch.empty(max(int(getattr(sz, f)), 256), dtype=u8, device=self.device)
+                          for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch")}
+        self.host_store = torch.empty(int(sz.host), dtype=u8).pin_memory()
+        tb = L.TierBuffers(*[self.tier_bufs[f].data_ptr() for f in ("cache", "map", "owner", "ref", "freq", "ein",
+                                                                      "queue", "scratch")],
+                           self.host_store.data_ptr())
+        L.check(lib.svf_tier_enable(self._h, C.byref(tp), C.byref(tb), _stream()))
+        torch.cuda.synchronize(self.device)
+
+    def release_device_store(self) -> None:
+        """After enable_tier the device copy of the primary rows is not read;
+        free it (vectors() is unavailable afterwards)."""
+        self.vecs = None
+        torch.cuda.empty_cache()
+
+    def tier_map(self) -> torch.Tensor:
+        return self.tier_bufs["map"][: self.n_cap * 4].view(torch.int32)
+
+    def maintain(self, stream=None) -> int:
+        n = C.c_int64(0)
+        L.check(L.load().svf_tier_maintain(self._h, C.byref(n), _stream(stream)))
+        return int(n.value)
+
+    def theta(self) -> float:
+        return float(L.load().svf_tier_theta(self._h))
+
     def sync(self) -> None:
         L.check(L.load().svf_sync(self._h))
 
@@ -197,3 +233,67 @@ def knn(X: torch.Tensor, Q: torch.Tensor, k: int, metric: str = "l2", self_ids: 
     L.check(lib.svf_knn(_ptr(X), X.shape[0], X.shape[1], dt, L.IP if metric == "ip" else L.L2, _ptr(Q), nq,
                         _ptr(self_ids), k, _ptr(work), _ptr(ids), _ptr(dist), _stream(stream)))
     return ids, dist
+
+
+class Server:
+    """Continuous-batching request loop (svf_serve_*): submit searches,
+    inserts and deletes; poll completions with host timestamps."""
+
+    def __init__(self, ix: Index, max_inflight: int = 8, n_streams: int = 4, maintain_every: int = 64):
+        self.ix = ix
+        self.lib = L.load()
+        h = C.c_void_p()
+        cfg = L.ServeCfg(max_inflight, n_streams, maintain_every, 0)
+        with torch.cuda.device(ix.device):
+            L.check(self.lib.svf_serve_start(ix._h, C.byref(cfg), C.byref(h)))
+        self._s = h
+        self._keep = {}
+
+    @staticmethod
+    def now() -> float:
+        return float(L.load().svf_serve_now())
+
+    def _submit(self, r, keep):
+        self._keep[r.tag] = keep
+        L.check(self.lib.svf_serve_submit(self._s, C.byref(r)))
+
+    def search(self, tag: int, Q: torch.Tensor, cfg: SearchConfig, out_ids: torch.Tensor, out_dist: torch.Tensor,
+               t_arrival: float = 0.0):
+        prec = {None: L.U8 if self.ix.dtype == "u8" else L.F32, "bf16": L.BF16, "fp8": L.FP8}[cfg.precision]
+        import math
+        z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
+        sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
+                            cfg.hash_log2, None, cfg.seed, None, None, None, cfg.t_every, 0)
+        r = L.Request(L.OP_SEARCH, Q.shape[0], Q.data_ptr(), sp, out_ids.data_ptr(), out_dist.data_ptr(), None, 0, 0,
+                      tag, t_arrival)
+        self._submit(r, (Q, out_ids, out_dist, cfg))
+
+    def insert(self, tag: int, X: torch.Tensor, L_ins: int = 64, T_ins: int = 32, out_ids=None, t_arrival: float = 0.0):
+        r = L.Request(L.OP_INSERT, X.shape[0], X.data_ptr(), L.SearchParams(), None, None, _ptr(out_ids), L_ins,
+                      T_ins, tag, t_arrival)
+        self._submit(r, (X, out_ids))
+        self.ix.n_used += X.shape[0]
+
+    def delete(self, tag: int, ids: torch.Tensor, t_arrival: float = 0.0):
+        r = L.Request(L.OP_DELETE, ids.numel(), ids.data_ptr(), L.SearchParams(), None, None, None, 0, 0, tag,
+                      t_arrival)
+        self._submit(r, (ids,))
+
+    def poll(self, max_n: int = 4096) -> list[dict]:
+        buf = (L.Completion * max_n)()
+        n = C.c_int32(0)
+        L.check(self.lib.svf_serve_poll(self._s, buf, max_n, C.byref(n)))
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._keep.pop(c.tag, None)
+            out.append({f: getattr(c, f) for f, _ in L.Completion._fields_})
+        return out
+
+    def drain(self, timeout: float = 600.0) -> None:
+        L.check(self.lib.svf_serve_drain(self._s, timeout))
+
+    def stop(self) -> None:
+        if self._s:
+            L.check(self.lib.svf_serve_stop(self._s))
+            self._s = None

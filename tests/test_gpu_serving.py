@@ -1,0 +1,222 @@
+"""Serving form: tiered store (device cache over pinned host rows with WAVP
+placement) and the continuous-batching request loop (C ABI)."""
+import numpy as np
+import pytest
+
+import synth
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def svf():
+    import paper_2601_08528_b300 as svf
+    svf.load()
+    return svf
+
+
+def built(svf, mix, n, n_cap, R=32, metric="l2", seed=701, max_batch=None):
+    X = synth.sample(mix, n_cap, seed)
+    ix = svf.Index(X.shape[1], n_cap, dtype="u8" if X.dtype == np.uint8 else "f32", metric=metric, R=R,
+                   max_batch=max_batch or n)
+    ix.build(torch.from_numpy(X[:n]).cuda())
+    return X, ix
+
+
+def test_tiered_search_equals_device_search(svf):
+    X, ix = built(svf, "u8", 6000, 6000, R=64)
+    Q = torch.from_numpy(synth.sample("u8", 500, 702)).cuda()
+    cfg = svf.SearchConfig(k=10, L=64, T=48, seed=3)
+    ids0, d0 = ix.search(Q, cfg)
+    ix.enable_tier(M=600, theta0=0.5, promote_batch=256, sweep=4, qcap=4096)
+    ix.release_device_store()
+    ix.stats_reset()
+    ids1, d1 = ix.search(Q, cfg)
+    assert torch.equal(ids0, ids1) and torch.equal(d0, d1)
+    s = ix.stats()
+    assert s["cache_hits"] > 0 and s["cache_misses"] > 0
+    promoted = ix.maintain()
+    assert promoted > 0
+    assert int((ix.tier_map()[:6000] >= 0).sum().item()) == 600
+    ids2, d2 = ix.search(Q, cfg)
+    assert torch.equal(ids0, ids2) and torch.equal(d0, d2)
+
+
+
+def test_promotion_follows_a_skewed_workload(svf):
+    """Queries from one mixture component: the rows they touch get promoted
+    and the hit rate of the same workload rises (Eq. 2 / Alg. 2 at work)."""
+    lab = []
+    X = synth.sample("tiny", 8000, 741, labels_out=lab)
+    ix = svf.Index(128, 8000, dtype="f32", metric="l2", R=32, max_batch=8000)
+    ix.build(torch.from_numpy(X).cuda())
+    ql = []
+    Qall = synth.sample("tiny", 4000, 742, labels_out=ql)
+    Q = torch.from_numpy(Qall[ql[0] == 3]).cuda()
+    cfg = svf.SearchConfig(k=10, L=64, T=32)
+    ids0, d0 = ix.search(Q, cfg)
+    ix.enable_tier(M=1200, theta0=1.0, promote_batch=512, sweep=4, qcap=8192)
+    ix.release_device_store()
+
+    def hit_rate():
+        ix.stats_reset()
+        ids, d = ix.search(Q, cfg)
+        assert torch.equal(ids, ids0) and torch.equal(d, d0)
+        s = ix.stats()
+        return s["cache_hits"] / (s["cache_hits"] + s["cache_misses"])
+
+    r0 = hit_rate()
+    for _ in range(4):
+        ix.maintain()
+        r = hit_rate()
+    assert r > r0 + 0.2, (r0, r)
+
+
+def test_tiered_updates_equal_device_updates(svf):
+    X, a = built(svf, "u8", 3000, 3600, R=32, max_batch=3000)
+    _, b = built(svf, "u8", 3000, 3600, R=32, max_batch=3000)
+    b.enable_tier(M=300, theta0=0.5, promote_batch=128, qcap=2048)
+    b.release_device_store()
+    Q = torch.from_numpy(synth.sample("u8", 200, 711)).cuda()
+    cfg = svf.SearchConfig(k=10, L=64, T=32)
+    for step in range(3):
+        xi = torch.from_numpy(X[3000 + 200 * step:3200 + 200 * step]).cuda()
+        a.insert(xi, L_ins=64, T_ins=32)
+        b.insert(xi, L_ins=64, T_ins=32)
+        dels = torch.from_numpy(synth.pick_live_ids(a.n_used, None, 150, 712 + step).view(np.int32)).cuda()
+        assert a.delete(dels) == b.delete(dels)
+        b.maintain()
+        assert torch.equal(a.graph[:a.n_used], b.graph[:b.n_used])
+        ia, da = a.search(Q, cfg)
+        ib, db = b.search(Q, cfg)
+        assert torch.equal(ia, ib) and torch.equal(da, db)
+
+
+@pytest.mark.parametrize("ein_mode", ["freq", "indegree"])
+def test_wavp_round_matches_oracle(svf, orc, ein_mode):
+    n, M = 4000, 256
+    X, ix = built(svf, "u8", n, n, R=32)
+    ix.enable_tier(M=M, theta0=1e9, promote_batch=64, sweep=4, qcap=1024)
+    rng = np.random.default_rng(721)
+    # a crafted state: 200 cached ids, some referenced slots, a queue of 150
+    owner = np.full(M, -1, np.int32)
+    cached = rng.choice(n, 200, replace=False)
+    slots = rng.choice(M, 200, replace=False)
+    owner[slots] = cached
+    map_ = np.full(n, -1, np.int32)
+    map_[cached] = slots
+    ref = (rng.random(M) < 0.3).astype(np.uint8)
+    if ein_mode == "freq":
+        freq = rng.permutation(n).astype(np.uint32)   # distinct F, exact in fp32 and fp64
+        ein = np.zeros(n, np.uint32)
+    else:
+        freq = np.zeros(n, np.uint32)
+        ein = rng.integers(0, 60, n).astype(np.uint32)
+    queue = rng.choice(np.setdiff1d(np.arange(n), cached), 150, replace=False).astype(np.uint32)
+    tb = ix.tier_bufs
+    tb["owner"][:M * 4].view(torch.int32).copy_(torch.from_numpy(owner))
+    tb["map"][:n * 4].view(torch.int32).copy_(torch.from_numpy(map_))
+    tb["ref"][:M].copy_(torch.from_numpy(ref))
+    fq = freq.copy()
+    fq[queue] |= np.uint32(1 << 31)  # queued ids carry the queued flag
+    tb["freq"][:n * 4].view(torch.int32).copy_(torch.from_numpy(fq.view(np.int32)))
+    tb["ein"][:n * 4].view(torch.int32).copy_(torch.from_numpy(ein.view(np.int32)))
+    tb["queue"][:150 * 4].view(torch.int32).copy_(torch.from_numpy(queue.view(np.int32)))
+    ix.status.view(torch.int64)[11] = 150
+    torch.cuda.synchronize()
+    got = ix.maintain()
+    p, e = orc.wavp_round(map_, owner, ref, freq, ein, queue, 64, 0, 256, 0.6, 0.4)
+    assert got == p
+    np.testing.assert_array_equal(tb["owner"][:M * 4].view(torch.int32).cpu().numpy(), owner)
+    np.testing.assert_array_equal(tb["map"][:n * 4].view(torch.int32).cpu().numpy(), map_)
+    np.testing.assert_array_equal(tb["ref"][:M].cpu().numpy(), ref)
+    # queued flags cleared, counts kept; the cache holds the host rows
+    f = tb["freq"][:n * 4].view(torch.int32).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(f, freq)
+    cache = tb["cache"][:M * 128].view(M, 128).cpu().numpy()
+    promoted_slots = np.where(np.isin(owner, queue))[0]
+    assert len(promoted_slots) == p
+    for s in promoted_slots:
+        np.testing.assert_array_equal(cache[s], X[owner[s]])
+
+
+def _trace(rng, n_req, n_start, X, n_base):
+    """A mixed request stream: search batches log-uniform in [1, 256],
+    inserts and deletes (roughly 90:9:1)."""
+    reqs, n_used, nxt = [], n_base, n_base
+    for i in range(n_req):
+        u = rng.random()
+        if u < 0.09 and nxt + 100 <= len(X):
+            reqs.append(("insert", nxt, 100))
+            nxt += 100
+        elif u < 0.10:
+            reqs.append(("delete", int(rng.integers(0, 1 << 30)), 40))
+        else:
+            reqs.append(("search", int(rng.integers(0, 1 << 30)), int(np.exp(rng.uniform(0, np.log(256))))))
+    return reqs
+
+
+@pytest.mark.parametrize("tiered", [False, True])
+def test_server_results_equal_alone(svf, tiered):
+    """Each search served in the mix equals the same search run alone on the
+    index state of its epoch; updates advance the epoch in submission order."""
+    n0, ncap = 8000, 12000
+    X, ix = built(svf, "u8", n0, ncap, R=32, max_batch=8000)
+    _, ref_ix = built(svf, "u8", n0, ncap, R=32, max_batch=8000)
+    if tiered:
+        ix.enable_tier(M=1500, theta0=0.5, promote_batch=256, qcap=4096)
+        ix.release_device_store()
+    rng = np.random.default_rng(731)
+    reqs = _trace(rng, 120, n0, X, n0)
+    srv = svf.Server(ix, max_inflight=6, n_streams=4, maintain_every=4)
+    cfg = svf.SearchConfig(k=10, L=64, T=32)
+    outs = {}
+    deleted = set()
+    n_used = n0
+    dev_inputs = []
+    for tag, (op, a, b) in enumerate(reqs):
+        if op == "search":
+            Q = torch.from_numpy(synth.sample("u8", b, 10_000 + tag)).cuda()
+            oi = torch.empty((b, 10), dtype=torch.int32, device="cuda")
+            od = torch.empty((b, 10), dtype=torch.int32, device="cuda")
+            srv.search(tag, Q, cfg, oi, od)
+            outs[tag] = (Q, oi, od)
+        elif op == "insert":
+            xi = torch.from_numpy(X[a:a + b]).cuda()
+            srv.insert(tag, xi, L_ins=64, T_ins=32)
+            dev_inputs.append((tag, "insert", xi))
+            n_used += b
+        else:
+            ids = synth.pick_live_ids(n_used, np.array(sorted(deleted), np.int64), b, a)
+            deleted.update(ids.tolist())
+            di = torch.from_numpy(ids.view(np.int32)).cuda()
+            srv.delete(tag, di)
+            dev_inputs.append((tag, "delete", di))
+    srv.drain(300)
+    comps = {c["tag"]: c for c in srv.poll(10000)}
+    srv.stop()
+    assert len(comps) == len(reqs) and all(c["status"] == 0 for c in comps.values())
+    # replay alone, in order
+    upd = {t: (k, v) for t, k, v in dev_inputs}
+    epoch = 0
+    for tag, (op, a, b) in enumerate(reqs):
+        c = comps[tag]
+        assert c["t_done"] >= c["t_start"] > 0
+        if op == "search":
+            assert c["epoch"] == epoch
+            Q, oi, od = outs[tag]
+            ri, rd = ref_ix.search(Q, cfg)
+            assert torch.equal(ri, oi) and torch.equal(rd, od), f"request {tag}"
+        else:
+            kind, v = upd[tag]
+            if kind == "insert":
+                ref_ix.insert(v, L_ins=64, T_ins=32)
+            else:
+                ref_ix.delete(v)
+            epoch += 1
+            assert c["epoch"] == epoch
+    torch.cuda.synchronize()
+    assert torch.equal(ix.graph[:n_used], ref_ix.graph[:n_used])
