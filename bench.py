@@ -58,13 +58,18 @@ def parse():
     ap.add_argument("--ntrain", type=int, default=200_000)
     ap.add_argument("--target", type=float, default=0.95)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-rate", type=float, default=500.0, help="requests/s of the serving stream (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--workload", default="unit96-10M", choices=["unit96-10M", "serve128-50M"])
+    ap.add_argument("--serve-rates", default="250,500,1000,2000")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- setup
 def build_index(svf, torch, X, log_t):
     n = X.shape[0]
-    ix = svf.Index(96, n, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"), max_batch=MAX_BATCH)
+    # headroom for the serving stream's inserts
+    ix = svf.Index(96, n + 300_000, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"), max_batch=MAX_BATCH)
     n0 = min(N_BOOT, n)
     t = time.time()
     ix.build(torch.from_numpy(X[:n0]).cuda())
@@ -151,6 +156,85 @@ def train_stops(torch, svf, ix, Qtr, gt_cal, ncal, precisions):
             log(f"  stop net {prec} L={L} T={T}: loss={net.loss:.4f} samples={ids.numel()} tau={tau} "
                 f"recall fixed={r0:.4f} stop={r1:.4f}")
     return nets
+
+
+# ---------------------------------------------------------------- serving
+def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zipf_s=1.1, max_inflight=8,
+                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048):
+    """Open-loop Poisson stream at `rate` requests/s for `duration` s through
+    the continuous-batching server: 90:9:1 search:insert:delete requests,
+    batch sizes floor(exp(U[0, ln max_batch])), query components ~ Zipf(s).
+    Returns latency percentiles (ms) per op over the requests that arrived
+    after `warm` s, query and insert throughput, and cache counters."""
+    rng = np.random.default_rng(seed)
+    m = synth.MIXTURES[mix]
+    arr, ops, sizes = [], [], []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        arr.append(t)
+        u = rng.random()
+        ops.append(0 if u < 0.90 else (1 if u < 0.99 else 2))
+        sizes.append(max(1, min(max_batch, int(np.exp(rng.uniform(0, np.log(max_batch)))))))
+    nq = sum(sz for o, sz in zip(ops, sizes) if o == 0)
+    Qall = torch.from_numpy(synth.sample_chunked(m, max(nq, 1), seed + 1,
+                                                 component_sampler=synth.zipf_components(m.n_centres, zipf_s,
+                                                                                          seed + 2))).cuda()
+    k = cfg.k
+    ids_out = torch.empty((max(nq, 1), k), dtype=torch.int32, device="cuda")
+    d_out = torch.empty((max(nq, 1), k), dtype=torch.int32 if m.dtype == "u8" else torch.float32, device="cuda")
+    srv = svf.Server(ix, max_inflight=max_inflight, n_streams=n_streams, maintain_every=maintain_every)
+    ix.stats_reset()
+    qo, io = 0, 0
+    n_used = ix.n_used
+    deleted = 0
+    t0 = svf.Server.now() + 0.5
+    for tag, (ta, op, sz) in enumerate(zip(arr, ops, sizes)):
+        if op == 0:
+            srv.search(tag, Qall[qo:qo + sz], cfg, ids_out[qo:qo + sz], d_out[qo:qo + sz], t_arrival=t0 + ta)
+            qo += sz
+        elif op == 1:
+            sz = min(sz, X_ins.shape[0] - io, ix.n_cap - n_used)
+            if sz <= 0:
+                continue
+            srv.insert(tag, torch.from_numpy(X_ins[io:io + sz]).cuda(), L_ins=L_ins, T_ins=T_ins, t_arrival=t0 + ta)
+            io += sz
+            n_used += sz
+        else:
+            ids = torch.from_numpy(rng.integers(0, n_used, sz).astype(np.int32)).cuda()
+            srv.delete(tag, ids, t_arrival=t0 + ta)
+            deleted += sz
+    srv.drain(duration + 600)
+    comps = srv.poll(1 << 20)
+    srv.stop()
+    st = ix.stats()
+    lat = {0: [], 1: [], 2: []}
+    done_q = done_i = 0
+    t_first, t_last = None, None
+    for c in comps:
+        if c["t_arrival"] - t0 < warm:
+            continue
+        lat[c["op"]].append(1e3 * (c["t_done"] - c["t_arrival"]))
+        if c["op"] == 0:
+            done_q += c["count"]
+        elif c["op"] == 1:
+            done_i += c["count"]
+        t_first = c["t_arrival"] if t_first is None else min(t_first, c["t_arrival"])
+        t_last = c["t_done"] if t_last is None else max(t_last, c["t_done"])
+    span = max(t_last - t_first, 1e-9) if t_first is not None else 1.0
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v else None
+    names = {0: "search", 1: "insert", 2: "delete"}
+    out = {"rate_req_per_s": rate, "duration_s": duration, "warmup_s": warm, "requests": len(comps),
+           "qps": done_q / span, "inserts_per_s": done_i / span,
+           "latency_ms": {names[o]: {"p50": pct(v, 50), "p99": pct(v, 99), "n": len(v)} for o, v in lat.items()},
+           "cache_hit_rate": (st["cache_hits"] / max(1, st["cache_hits"] + st["cache_misses"]))
+           if st["cache_hits"] + st["cache_misses"] else None,
+           "promoted": st["promoted"], "evicted": st["evicted"]}
+    return out
 
 
 # ---------------------------------------------------------------- clocks
@@ -240,6 +324,57 @@ def oracle_qps(X, graph_np, Q, L, T, seconds):
     return m2 / dt, m2, orc.threads()
 
 
+# ---------------------------------------------------------------- serving workload (50M)
+def serve_main(a, svf, torch, log_t):
+    """The serving form at full size: n = 50M fp32 d=128 (squared L2), R = 32,
+    built on the GPU (exact build of 200K + inserts), then tiered: all rows in
+    pinned host memory behind an 8 GB device cache (15.6M rows) with WAVP
+    placement; an open-loop Poisson stream per offered rate."""
+    n = 50_000_000
+    X = synth.sample_chunked("serve128", n, 500)
+    log_t("data", X.shape)
+    ix = svf.Index(128, n + 2_000_000, dtype="f32", metric="l2", R=R, max_batch=MAX_BATCH)
+    ix.build(torch.from_numpy(X[:N_BOOT]).cuda())
+    while ix.n_used < n:
+        b = min(ix.n_used, MAX_BATCH, n - ix.n_used)
+        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=64, T_ins=48)
+    torch.cuda.synchronize()
+    log_t("built")
+    Qe = torch.from_numpy(synth.sample_chunked("serve128", 2000, 502)).cuda()
+    gt, _ = svf.knn(ix.vectors()[:n], Qe, K, "l2")
+    from paper_2601_08528_b300.learned import recall_at_k
+    op = None
+    for L, T in [(64, 64), (64, 96), (128, 64), (128, 96), (256, 128)]:
+        cfg = svf.SearchConfig(k=K, L=L, T=T)
+        r = recall_at_k(ix.search(Qe, cfg)[0], gt)
+        log_t(f"  L={L} T={T} recall={r:.4f}")
+        if r >= a.target:
+            op = (cfg, r)
+            break
+    cfg, rec = op if op else (svf.SearchConfig(k=K, L=256, T=128), float("nan"))
+    slots = int(8e9 // (128 * 4))
+    ix.enable_tier(M=slots, theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
+    ix.release_device_store()
+    del X
+    log_t("tiered", slots)
+    X_ins = synth.sample_chunked("serve128", 1_500_000, 503)
+    res = []
+    for i, rate in enumerate(float(x) for x in a.serve_rates.split(",")):
+        r = serve_stream(svf, torch, ix, "serve128", X_ins[i * 300_000:(i + 1) * 300_000], rate, a.serve_seconds,
+                         2.0, 510 + i, cfg)
+        res.append(r)
+        log_t("rate", rate, json.dumps(r))
+    p99 = [x["latency_ms"]["search"]["p99"] for x in res if x["latency_ms"]["search"]["p99"] is not None]
+    out = {"metric": "serving p99 search latency (ms) at offered load", "value": min(p99) if p99 else None,
+           "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+           "config": {"workload": "serve128-50M", "n": n, "d": 128, "R": R, "cache_rows": slots, "L": cfg.L,
+                      "T": cfg.T, "recall@10": rec, "mix": "90:9:1", "batch": "log-uniform 1..2048",
+                      "queries": "Zipf(1.1) over components"},
+           "rates": res}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- main
 def main():
     a = parse()
@@ -261,6 +396,8 @@ def main():
     def log_t(*x):
         log(f"[{time.time() - t0:7.1f}s]", *x)
 
+    if a.workload == "serve128-50M":
+        return serve_main(a, svf, torch, log_t)
     X = synth.sample_chunked("unit96", a.n, 300)
     Qe_np = synth.sample_chunked("unit96", a.nq, 302 + rank)
     log_t("data", X.shape)
@@ -399,6 +536,18 @@ def main():
         "gpu_launches": a.steps,
         "clocks": clk,
     }
+    # serving: the same index with its fp32 rows tiered behind a device cache
+    # of 31 % of them (the 8 GB : 25.6 GB ratio of the 50M serving workload),
+    # fp8 traversal resident, exact re-rank through the tier; an open-loop
+    # Poisson stream of uneven batches with inserts and deletes
+    if a.serve_rate > 0:
+        ix.enable_tier(M=int(a.n * 0.3125), theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
+        X_ins = synth.sample_chunked("unit96", 200_000, 305)
+        out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg)
+        out["serving"]["workload"] = ("unit96-10M tiered: fp32 rows in pinned host memory behind a 3.1M-row device "
+                                      "cache, fp8 traversal + exact re-rank, Zipf(1.1) queries, 90:9:1 mix, "
+                                      "batches log-uniform 1..2048")
+        log_t("serving", json.dumps(out["serving"]))
     # deletes (1% of the index, uniformly drawn live ids) with localized repair
     dels = torch.from_numpy(synth.pick_live_ids(a.n, None, a.n // 100, 304).view(np.int32)).cuda()
     torch.cuda.synchronize()

@@ -239,7 +239,10 @@ int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, 
  * decay_every misses, and adapts theta to the miss rate (Sec. 4.4).  It must
  * not run while a search or update on the index is in flight.
  * Enable warms the cache with the highest in-degree rows (cold start).  The
- * device copy of the primary store is not read afterwards. */
+ * device copy of the primary store is not read afterwards; low-precision
+ * copies (lowp) stay whole in device memory and are encoded from the
+ * inserted rows, so BF16/FP8 traversal reads no host memory and only the
+ * exact re-rank goes through the tier. */
 typedef struct {
     int64_t M;              /* cache slots */
     uint32_t qcap;          /* promotion queue capacity (<= 16384) */

@@ -146,9 +146,11 @@ int svf_attach(svf_index *h, int64_t n_used) {
     return SVF_OK;
 }
 
-static int encode_lowp(svf_index *h, int64_t row0, int64_t m, cudaStream_t st) {
+// Low-precision copies of rows [row0, row0+m); `src` holds those rows
+// (device fp32), by default the primary store.
+static int encode_lowp(svf_index *h, int64_t row0, int64_t m, cudaStream_t st, const float *src = nullptr) {
     if (!h->p.lowp || m == 0) return SVF_OK;
-    const float *src = reinterpret_cast<const float *>(h->b.vecs) + row0 * h->p.d;
+    if (!src) src = reinterpret_cast<const float *>(h->b.vecs) + row0 * h->p.d;
     if (h->p.lowp & 1)
         CUDA_TRY(launch_encode_bf16(src, m, h->p.d, reinterpret_cast<uint16_t *>(h->b.vecs_bf16) + row0 * h->p.d, st));
     if (h->p.lowp & 2)
@@ -285,7 +287,7 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     uint8_t *dst = h->tier.on ? h->tier.host : reinterpret_cast<uint8_t *>(h->b.vecs);
     CUDA_TRY(cudaMemcpyAsync(dst + n0 * P.pitch, X, (size_t)m * P.pitch,
                              h->tier.on ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-    int rc = h->tier.on ? SVF_OK : encode_lowp(h, n0, m, st);
+    int rc = encode_lowp(h, n0, m, st, h->tier.on ? reinterpret_cast<const float *>(X) : nullptr);
     if (rc) return rc;
     uint64_t *pool = reinterpret_cast<uint64_t *>(h->wsp(h->ws.region + h->ws.pool));
     uint32_t *rows = reinterpret_cast<uint32_t *>(h->wsp(h->ws.region + h->ws.rows));

@@ -245,6 +245,9 @@ int svf_serve_stop(svf_server *s) {
     if (!s) return svf::fail(SVF_EINVAL, "null server");
     s->stop = true;
     if (s->worker.joinable()) s->worker.join();
+    for (auto st : s->streams) cudaStreamSynchronize(st);
+    cudaStreamSynchronize(s->upd);
+    s->h->last = nullptr;  // the index's calls went to the server's streams
     for (auto st : s->streams) cudaStreamDestroy(st);
     for (auto ev : s->free_ev) cudaEventDestroy(ev);
     cudaStreamDestroy(s->upd);

@@ -516,17 +516,30 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
             for (int m = 16; m > 0; m >>= 1) nhit += __shfl_xor_sync(kFull, nhit, m);
             if (nhit > 0 && lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(nhit * R.copy_bytes));
             __syncwarp();
-            for (int j = lane; j < cnt; j += 32) {
+            uint32_t mmask = 0;  // this lane's missed rows (j = lane + 32 t)
+            for (int j = lane, t = 0; j < cnt; j += 32, t++) {
                 const uint32_t id = list[i0 + j];
                 const int32_t slot = __ldg(R.map + id);
-                uint8_t *dst = S.buf + (size_t)j * R.copy_bytes;
                 if (slot >= 0) {
-                    bulk_g2s(dst, R.base + (int64_t)slot * R.pitch, R.copy_bytes, S.mbar);
+                    bulk_g2s(S.buf + (size_t)j * R.copy_bytes, R.base + (int64_t)slot * R.pitch, R.copy_bytes, S.mbar);
                     tier->ref[slot] = 1;
                 } else {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(R.host + (int64_t)id * R.pitch);
-                    for (int c = 0; c < R.copy_bytes / 16; c++) reinterpret_cast<uint4 *>(dst)[c] = src[c];
+                    mmask |= 1u << t;
                     tier_miss(*tier, id);
+                }
+            }
+            // missed rows: the whole warp copies them from host memory, every
+            // 16-byte chunk of every missed row spread over the lanes
+            const int cpr = R.copy_bytes / 16;
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const uint32_t miss = __ballot_sync(kFull, (mmask >> (j0 >> 5)) & 1u);
+                const int nm = __popc(miss);
+#pragma unroll 4
+                for (int e = lane; e < nm * cpr; e += 32) {
+                    const int r = e / cpr, c = e - r * cpr;
+                    const int j = j0 + __fns(miss, 0, r + 1);  // position of the r-th missed row
+                    const uint4 *src = reinterpret_cast<const uint4 *>(R.host + (int64_t)list[i0 + j] * R.pitch);
+                    reinterpret_cast<uint4 *>(S.buf + (size_t)j * R.copy_bytes)[c] = src[c];
                 }
             }
             if (hits) *hits += nhit;

@@ -208,7 +208,6 @@ int svf_tier_buffer_sizes(const svf_params *p, const svf_tier_params *tp, svf_ti
 int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buffers *tb, void *stream) {
     if (!h || !tp || !tb) return fail(SVF_EINVAL, "null arguments");
     if (h->tier.on) return fail(SVF_EINVAL, "the store is already tiered");
-    if (h->p.lowp) return fail(SVF_EINVAL, "a tiered store keeps no low-precision copies (lowp must be 0)");
     svf_tier_sizes sz;
     int rc = svf_tier_buffer_sizes(&h->p, tp, &sz);
     if (rc) return rc;

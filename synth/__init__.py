@@ -17,7 +17,9 @@ shapes and value ranges of the workloads:
                 descriptors such as Deep1B's have a low intrinsic dimension;
                 a mixture of 4,096 isotropic 96-d blobs would instead split
                 into thousands of disconnected neighbourhoods.
-* ``serve128``  n=50,000,000 fp32, d=128, 16,384 centres U[-5,5]^d, sigma=1.
+* ``serve128``  n=50,000,000 fp32, d=128, 16,384 components built like
+                ``unit96`` (16-dimensional latent structure, 0.02 isotropic
+                noise) but not normalised (squared L2).
 
 Every draw is keyed by an explicit seed so a test, the oracle and a GPU run
 see byte-identical inputs.
@@ -54,7 +56,7 @@ MIXTURES = {
     "u8": Mixture("u8", 128, 1024, "u8", "uniform", 32.0, 224.0, 20.0, 201),
     "unit96": Mixture("unit96", 96, 4096, "f32", "latent", 0.0, 0.0, 1.0, 301, normalize=True,
                       latent_dim=16, iso_sigma=0.02),
-    "serve128": Mixture("serve128", 128, 16384, "f32", "uniform", -5.0, 5.0, 1.0, 501),
+    "serve128": Mixture("serve128", 128, 16384, "f32", "latent", 0.0, 0.0, 1.0, 501, latent_dim=16, iso_sigma=0.02),
 }
 
 

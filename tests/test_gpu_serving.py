@@ -220,3 +220,27 @@ def test_server_results_equal_alone(svf, tiered):
             assert c["epoch"] == epoch
     torch.cuda.synchronize()
     assert torch.equal(ix.graph[:n_used], ref_ix.graph[:n_used])
+
+
+def test_tiered_lowp_rerank_equals_device(svf):
+    """BF16/FP8 copies stay whole in device memory; the exact re-rank reads
+    the fp32 rows through the tier: results equal the untiered index, before
+    and after inserts (their low-precision rows are encoded from the input)."""
+    X = synth.sample("unit96", 5000, 751)
+    a = svf.Index(96, 5000, dtype="f32", metric="ip", R=32, lowp=("fp8",), max_batch=4000)
+    b = svf.Index(96, 5000, dtype="f32", metric="ip", R=32, lowp=("fp8",), max_batch=4000)
+    for ix in (a, b):
+        ix.build(torch.from_numpy(X[:4000]).cuda())
+    b.enable_tier(M=400, theta0=0.5, promote_batch=128, qcap=2048)
+    b.release_device_store()
+    Q = torch.from_numpy(synth.sample("unit96", 300, 752)).cuda()
+    cfg = svf.SearchConfig(k=10, L=64, T=48, precision="fp8", rerank=True)
+    for step in range(2):
+        ia, da = a.search(Q, cfg)
+        ib, db = b.search(Q, cfg)
+        assert torch.equal(ia, ib) and torch.equal(da, db)
+        xi = torch.from_numpy(X[4000 + 500 * step:4500 + 500 * step]).cuda()
+        a.insert(xi)
+        b.insert(xi)
+        b.maintain()
+    assert torch.equal(a.vecs_fp8[:5000 * 128], b.vecs_fp8[:5000 * 128])
