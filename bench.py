@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=500.0, help="requests/s of the serving stream (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
     ap.add_argument("--workload", default="unit96-10M", choices=["unit96-10M", "serve128-50M"])
-    ap.add_argument("--serve-rates", default="250,500,1000,2000")
+    ap.add_argument("--serve-rates", default="25,50,100,200")
+    ap.add_argument("--serve-form", default="fp32", choices=["fp32", "fp8"],
+                    help="serving traversal: fp32 rows through the tier, or a resident fp8 copy + exact re-rank")
     return ap.parse_args()
 
 
@@ -333,7 +335,8 @@ def serve_main(a, svf, torch, log_t):
     n = 50_000_000
     X = synth.sample_chunked("serve128", n, 500)
     log_t("data", X.shape)
-    ix = svf.Index(128, n + 2_000_000, dtype="f32", metric="l2", R=R, max_batch=MAX_BATCH)
+    lowp = ("fp8",) if a.serve_form == "fp8" else ()
+    ix = svf.Index(128, n + 2_000_000, dtype="f32", metric="l2", R=R, lowp=lowp, max_batch=MAX_BATCH)
     ix.build(torch.from_numpy(X[:N_BOOT]).cuda())
     while ix.n_used < n:
         b = min(ix.n_used, MAX_BATCH, n - ix.n_used)
@@ -344,14 +347,14 @@ def serve_main(a, svf, torch, log_t):
     gt, _ = svf.knn(ix.vectors()[:n], Qe, K, "l2")
     from paper_2601_08528_b300.learned import recall_at_k
     op = None
-    for L, T in [(64, 64), (64, 96), (128, 64), (128, 96), (256, 128)]:
-        cfg = svf.SearchConfig(k=K, L=L, T=T)
+    for L, T in [(64, 64), (64, 96), (128, 64), (128, 96), (256, 128), (256, 192)]:
+        cfg = svf.SearchConfig(k=K, L=L, T=T, precision=a.serve_form if lowp else None, rerank=bool(lowp))
         r = recall_at_k(ix.search(Qe, cfg)[0], gt)
         log_t(f"  L={L} T={T} recall={r:.4f}")
         if r >= a.target:
             op = (cfg, r)
             break
-    cfg, rec = op if op else (svf.SearchConfig(k=K, L=256, T=128), float("nan"))
+    cfg, rec = op if op else (cfg, r)
     slots = int(8e9 // (128 * 4))
     ix.enable_tier(M=slots, theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
     ix.release_device_store()
@@ -367,7 +370,8 @@ def serve_main(a, svf, torch, log_t):
     p99 = [x["latency_ms"]["search"]["p99"] for x in res if x["latency_ms"]["search"]["p99"] is not None]
     out = {"metric": "serving p99 search latency (ms) at offered load", "value": min(p99) if p99 else None,
            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
-           "config": {"workload": "serve128-50M", "n": n, "d": 128, "R": R, "cache_rows": slots, "L": cfg.L,
+           "config": {"workload": "serve128-50M", "form": a.serve_form, "n": n, "d": 128, "R": R,
+                      "cache_rows": slots, "L": cfg.L,
                       "T": cfg.T, "recall@10": rec, "mix": "90:9:1", "batch": "log-uniform 1..2048",
                       "queries": "Zipf(1.1) over components"},
            "rates": res}
