@@ -18,6 +18,10 @@
 
 #include "svf_dev.cuh"
 #include "svf_internal.h"
+
+#ifndef SVF_SEARCH_MINB
+#define SVF_SEARCH_MINB 6  // resident CTAs of 4 warps per SM the register budget aims for
+#endif
 #include "svf_mlp.h"
 
 namespace svf {
@@ -79,7 +83,7 @@ __device__ __forceinline__ float pool_dist(const uint64_t (&pool)[LW], int e, in
 }
 
 template <int DT, int R, int LW, bool LEARN>
-__global__ void __launch_bounds__(kSearchWarps * 32) search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_kernel(const SearchArgs a) {
     constexpr int L = 32 * LW;
     constexpr int S = R / 32;  // graph ids per lane
     extern __shared__ __align__(16) uint8_t smem[];
