@@ -325,6 +325,18 @@ int svf_serve_poll(svf_server *s, svf_completion *out, int max, int *n_out);
 int svf_serve_drain(svf_server *s, double timeout_s);
 int svf_serve_stop(svf_server *s);
 
+/* Exact kNN on the tensor cores (fp32 store and queries, d <= 128 multiple
+ * of 16, k <= 32): bf16 tcgen05 GEMM tiles with TMEM accumulators select 48
+ * approximate candidates per query and database slice, which are re-scored
+ * exactly in fp32; a per-query certificate (bf16 error bound) proves that no
+ * row was missed, and queries that fail it are recomputed by the SIMT scan.
+ * scratch: device, svf_knn_tc_scratch_bytes(n, nq, d, k) bytes.
+ * *out_fallback (host, optional) = queries recomputed.  Synchronises. */
+size_t svf_knn_tc_scratch_bytes(int64_t n, int64_t nq, int32_t d, int32_t k);
+int svf_knn_tc(const float *X, int64_t n, int32_t d, int32_t metric, const float *Q, int64_t nq, int32_t k,
+               void *scratch, size_t scratch_bytes, uint32_t *out_ids, float *out_dist, int64_t *out_fallback,
+               void *stream);
+
 /* ---- allocation-free variant of svf_knn (the paper has no counterpart).
  * For callers that cannot call cudaMalloc -- a plugin or custom call inside
  * a host framework whose memory manager owns the device's memory, or a

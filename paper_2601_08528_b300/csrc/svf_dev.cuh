@@ -446,7 +446,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr uint32_t kWaitLimit = 1u << 26;  // bounded wait on a staging barrier
+constexpr uint32_t kWaitLimit = 1u << 22;  // bounded wait on an mbarrier (each try_wait may also block briefly)
 
 struct Stage {
     uint8_t *buf;     // per-warp buffer (16-byte aligned)

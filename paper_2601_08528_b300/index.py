@@ -297,3 +297,21 @@ class Server:
         if self._s:
             L.check(self.lib.svf_serve_stop(self._s))
             self._s = None
+
+
+def knn_tc(X: torch.Tensor, Q: torch.Tensor, k: int, metric: str = "l2", stream=None):
+    """Exact kNN on the tensor cores (fp32, d <= 128, k <= 32).  Returns
+    (ids, dists, number of queries recomputed by the SIMT fallback)."""
+    lib = L.load()
+    X = X.contiguous()
+    Q = Q.contiguous()
+    n, d = X.shape
+    nq = Q.shape[0]
+    nbytes = int(lib.svf_knn_tc_scratch_bytes(n, nq, d, k))
+    scratch = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=X.device)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    fb = C.c_int64(0)
+    L.check(lib.svf_knn_tc(_ptr(X), n, d, L.IP if metric == "ip" else L.L2, _ptr(Q), nq, k, _ptr(scratch), nbytes,
+                           _ptr(ids), _ptr(dist), C.byref(fb), _stream(stream)))
+    return ids, dist, int(fb.value)
