@@ -2,25 +2,35 @@
 // (ground truth, Sec. 6.1 "exhaustive linear scan"), for fp32 stores with
 // d <= 128.
 //
-// 1. Rows and queries are rounded to bf16 (zero-padded to 128 columns).
-// 2. tc_knn_kernel: a CTA owns 128 queries and one slice of the database.
-//    TMA loads 128-byte-swizzled tiles (queries once, 256 database rows per
-//    stage, two stages); one thread issues tcgen05.mma (kind::f16, bf16 in,
-//    fp32 accumulate, M=128, N=256, K=16) into a double-buffered TMEM
-//    accumulator; the four warps read their 32 TMEM lanes (= queries) with
-//    tcgen05.ld and keep each query's 48 best approximate distances.  The
-//    MMA of tile t+1 runs while tile t is scanned.
-// 3. rescore_kernel: per query, the candidates of all slices get exact fp32
+// 1. Rows and queries are rounded to bf16, zero-padded to a multiple of 32
+//    columns (one 64-byte swizzle atom per 32 columns).
+// 2. tc_knn_kernel: a CTA owns 128 queries and one slice of the database,
+//    in a warp-specialised pipeline linked by mbarriers.  A producer warp
+//    TMA-loads 256-row database tiles into a ring of shared-memory stages;
+//    an MMA warp issues tcgen05.mma (kind::f16, bf16 in, fp32 accumulate,
+//    M=128, N=256, K=16) for each tile into one of two TMEM accumulator
+//    buffers; eight epilogue warps (two per TMEM lane group, one per column
+//    half) read a buffer with tcgen05.ld, release it, and keep each query's
+//    16 best approximate distances per half: a max tree over 32 columns
+//    tests them against the lane's current 16th, and only when a lane of
+//    the warp beats it are the passing columns appended to a pending buffer
+//    and merged, all lanes at once, into the sorted lists.  For large sets a
+//    first pass of the same kernel over every 32nd tile gives each query a
+//    starting threshold (its 16th best in that sample), so the lists start
+//    near their final values and few chunks take the append path.
+// 3. rescore_kernel: per query, the candidates of all lists get exact fp32
 //    distances and the best k by (distance, id) are kept.  A certificate
-//    checks the result: every row left out of a slice's candidates has an
-//    approximate distance at least that slice's 48th, and the bf16 error of
-//    a distance is at most c ||q|| ||x|| (c = 2^-7 + d 2^-24 for the
-//    products and the fp32 sums, doubled for L2), so if min_slice(48th) - eps
-//    exceeds the k-th exact distance no row can be missing.  Queries that
-//    fail it are recomputed by the SIMT kernel (knn.cu).
+//    checks the result: every row left out of a list has an approximate
+//    distance at least that list's 16th, and the bf16 error of a distance is
+//    at most c ||q|| ||x|| (two roundings of 2^-9 each per product, plus the
+//    fp32 sums; c = 0.0085 covers d <= 128 with margin, doubled for L2), so
+//    if min_list(16th) - eps exceeds the k-th exact distance no row can be
+//    missing.  Queries that fail it are recomputed by the SIMT kernel
+//    (knn.cu).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "index_impl.h"
@@ -28,22 +38,44 @@
 namespace svf {
 namespace {
 
-constexpr int TM = 128, TN = 128, KP = 128, KC = 48, THREADS = 128;
-constexpr int NS = 4;                  // database tile stages in flight
-constexpr int A_BYTES = TM * KP * 2;   // two 64-column swizzle atoms of 128 rows
-constexpr int B_STAGE = TN * KP * 2;   // two atoms of TN rows
-constexpr int LIST_BYTES = KC * TM * 8;
-constexpr int NBAR = 1 + NS + 2;       // A, B stages, MMA done (two TMEM halves)
-constexpr int SMEM_BYTES = 1024 + A_BYTES + NS * B_STAGE + LIST_BYTES + 8 * NBAR + 64;
-constexpr uint32_t kTmemCols = 2 * TN;
+constexpr int TM = 128, TN = 256, KP = 128;   // KP: largest padded dimension
+constexpr int KA = 32;                         // columns per 64-byte swizzle atom
+constexpr int HALVES = 2;                      // epilogue warps per TMEM lane group (column halves)
+constexpr int KC = 16;                         // candidates kept per (query, slice, half)
+constexpr int EPI_WARPS = 4 * HALVES;          // warps 0-7: epilogue; warp w reads lanes 32 (w % 4) ..
+constexpr int THREADS = (EPI_WARPS + 2) * 32;  // warp 8: TMA producer, warp 9: MMA issuer
+constexpr int NS_MAX = 8;                      // database tile stages in shared memory (as many as fit)
+constexpr int NT = 2;                          // accumulator buffers of TN columns in TMEM
+constexpr int BUF = 16;                        // pending candidates of one 16-column sub-chunk
+constexpr int A_ATOM = TM * KA * 2, B_ATOM = TN * KA * 2;
+constexpr int LIST_BYTES = HALVES * KC * TM * 8;
+constexpr int BUF_BYTES = HALVES * BUF * TM * 8;
+constexpr int NBAR = 1 + 2 * NS_MAX + 2 * NT;  // A; full/empty per stage; full/empty per TMEM buffer
+constexpr int BAR_BYTES = 1024;                 // barriers + TMEM address, rounded to keep B aligned
+static_assert(8 * NBAR + 4 <= BAR_BYTES, "barrier area");
+constexpr int SMEM_LIMIT = 232448;              // opt-in shared memory per block
+// layout: [align pad][A: TM x kp][lists][pending][barriers][ns stages of TN x kp]
+__host__ __device__ constexpr int smem_fixed(int kp) { return 1024 + TM * kp * 2 + LIST_BYTES + BUF_BYTES + BAR_BYTES; }
+__host__ __device__ constexpr int stage_bytes(int kp) { return TN * kp * 2; }
+static_assert(smem_fixed(KP) + 2 * stage_bytes(KP) <= SMEM_LIMIT, "two stages at the largest width");
+constexpr int kSeedStride = 64;            // seed pass reads one tile in 64
+constexpr int kSeedRank = 8;               // seed = 8th best of the sample (~512th of all rows)
+constexpr int64_t kSeedMinRows = 1 << 17;  // smaller sets skip the seed pass
+static_assert(kSeedRank <= HALVES * KC, "seed rank within the sample lists");
+constexpr uint32_t kTmemCols = NT * TN;
+static_assert(kTmemCols <= 512, "TMEM columns");
 
 struct TcArgs {
     int64_t n, nq;
     int64_t rows_per_split;
     int splits;
     int metric;
+    int atoms;           // padded dimension / KA
+    int ns;              // stages in the ring
+    int tile_stride;     // 1, or s > 1: every s-th tile only (the seed pass)
+    const float *seed;   // [nq] starting threshold per query, or null (+inf)
     const float *norms;  // ||x||^2 (L2)
-    float *cand_d;       // [nq][splits][KC]
+    float *cand_d;       // [nq][splits][HALVES][KC]
     uint32_t *cand_i;
     unsigned long long *status;
 };
@@ -56,11 +88,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
         : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(const void *p) {
+// UMMA shared-memory descriptor: K-major operand, 64-byte swizzle (rows of
+// 32 bf16), 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(const void *p) {
     const uint64_t addr = smem_u32(p);
-    return ((addr >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+    return ((addr >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
 // Instruction descriptor: kind::f16, bf16 x bf16 -> fp32, both K-major.
@@ -86,6 +118,30 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
+// max of 32 floats (as bit patterns) by a pairwise tree
+__device__ __forceinline__ float max32(const uint32_t *v) {
+    float m[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) m[i] = fmaxf(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int i = 0; i < w; i++) m[i] = fmaxf(m[i], m[i + w]);
+    return m[0];
+}
+
+// -(min of 32 floats)
+__device__ __forceinline__ float max32_neg(const uint32_t *v) {
+    float m[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) m[i] = fminf(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int i = 0; i < w; i++) m[i] = fminf(m[i], m[i + w]);
+    return -m[0];
+}
+
 #define TMEM_LD32(taddr, v)                                                                                           \
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
                  "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                        \
@@ -96,28 +152,57 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity) {
                    "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                                                                \
                  : "r"(taddr))
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Warp-specialised pipeline, linked by mbarriers (no block-wide barrier in
+// the loop):
+//   producer (warp 8)  TMA: database tile t -> stage t % ns
+//   MMA      (warp 9)  tile t x query tile -> TMEM buffer t % NT
+//   epilogue (0-7)     TMEM buffer -> registers, release the buffer, then
+//                      filter / append / merge into the per-query lists.
 __global__ void __launch_bounds__(THREADS, 1)
     tc_knn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     extern __shared__ uint8_t sm_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~(uintptr_t)1023);
+    const int ns = a.ns;
+    const uint32_t a_atom = (uint32_t)A_ATOM, b_atom = (uint32_t)B_ATOM, b_stage = (uint32_t)(a.atoms * B_ATOM);
     uint8_t *sA = sm;
-    uint8_t *sB = sm + A_BYTES;
-    float *ld = reinterpret_cast<float *>(sB + NS * B_STAGE);
-    uint32_t *li = reinterpret_cast<uint32_t *>(ld + KC * TM);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(li + KC * TM);  // 0: A, 1..NS: B stages, NS+1..NS+2: MMA done
-    uint64_t *mdone = bar + 1 + NS;
-    uint32_t *holder = reinterpret_cast<uint32_t *>(bar + NBAR);
-    __shared__ int s_err;
+    float *ld = reinterpret_cast<float *>(sm + a.atoms * A_ATOM);
+    uint32_t *li = reinterpret_cast<uint32_t *>(ld + HALVES * KC * TM);
+    float2 *buf = reinterpret_cast<float2 *>(li + HALVES * KC * TM);  // [HALVES][BUF][TM] pending (distance, row)
+    uint64_t *barA = reinterpret_cast<uint64_t *>(buf + HALVES * BUF * TM);
+    uint64_t *full = barA + 1, *empty = full + NS_MAX;       // stage s loaded / consumed by the MMA
+    uint64_t *tfull = empty + NS_MAX, *tempty = tfull + NT;  // TMEM buffer b accumulated / read out
+    uint32_t *holder = reinterpret_cast<uint32_t *>(tempty + NT);
+    uint8_t *sB = reinterpret_cast<uint8_t *>(barA) + BAR_BYTES;
+    __shared__ int s_err, s_nl, s_nc, s_nm;
+    volatile int *err = &s_err;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int qr = tid & (TM - 1), half = (tid >> 7) & (HALVES - 1);  // epilogue: query row, column half
+    float *lst_d = ld + half * KC * TM + qr;  // this thread's list, stride TM
+    uint32_t *lst_i = li + half * KC * TM + qr;
+    float2 *pend = buf + half * BUF * TM + qr;
     const int64_t q0 = (int64_t)blockIdx.x * TM;
     const int64_t r_begin = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t r_end = min(a.n, r_begin + a.rows_per_split);
-    const int ntiles = r_end > r_begin ? (int)((r_end - r_begin + TN - 1) / TN) : 0;
+    const int64_t span = (int64_t)TN * a.tile_stride;  // rows from one tile to the next
+    const int ntiles = r_end > r_begin ? (int)((r_end - r_begin + span - 1) / span) : 0;
 
     if (tid == 0) {
         s_err = 0;
-        for (int i = 0; i < NBAR; i++) mbar_init(bar + i, 1);
+        s_nl = s_nc = s_nm = 0;
+        mbar_init(barA, 1);
+        for (int i = 0; i < ns; i++) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, 1);
+        }
+        for (int i = 0; i < NT; i++) {
+            mbar_init(tfull + i, 1);
+            mbar_init(tempty + i, EPI_WARPS);
+        }
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
@@ -125,99 +210,174 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int j = 0; j < KC; j++) {
-        ld[j * TM + tid] = INFINITY;
-        li[j * TM + tid] = kEmpty;
-    }
+    // A list starts full of (seed, empty) entries: rows at or above the seed
+    // are never kept, and the list's KC-th value never exceeds the seed.
+    const float seed0 = (a.seed && q0 + qr < a.nq) ? a.seed[q0 + qr] : INFINITY;
+    if (warp < EPI_WARPS)
+        for (int j = 0; j < KC; j++) {
+            lst_d[j * TM] = seed0;
+            lst_i[j * TM] = kEmpty;
+        }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *holder;
-    float thr = INFINITY;
 
-    auto load_b = [&](int t) {  // tile t into stage t % NS
-        uint8_t *dst = sB + (t % NS) * B_STAGE;
-        const int y = (int)(r_begin + (int64_t)t * TN);
-        mbar_expect_tx(bar + 1 + t % NS, B_STAGE);
-        tma_load_2d(dst, &tmB, 0, y, bar + 1 + t % NS);
-        tma_load_2d(dst + B_STAGE / 2, &tmB, 64, y, bar + 1 + t % NS);
-    };
-    auto issue_mma = [&](int t) {  // tile t: stage t % NS, TMEM half t & 1
-        const uint8_t *b = sB + (t % NS) * B_STAGE;
-        const uint32_t d = tmem + (uint32_t)((t & 1) * TN);
-#pragma unroll
-        for (int kb = 0; kb < 2; kb++)
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                mma_bf16(d, sw128_desc(sA + kb * (A_BYTES / 2) + j * 32), sw128_desc(b + kb * (B_STAGE / 2) + j * 32),
-                         (kb | j) != 0);
-        mma_commit(mdone + (t & 1));
-    };
-
-    if (tid == 0 && ntiles > 0) {
-        mbar_expect_tx(bar, A_BYTES);
-        tma_load_2d(sA, &tmA, 0, (int)q0, bar);
-        tma_load_2d(sA + A_BYTES / 2, &tmA, 64, (int)q0, bar);
-        for (int t = 0; t < NS && t < ntiles; t++) load_b(t);
-        if (wait_bar(bar, 0) && wait_bar(bar + 1, 0)) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            issue_mma(0);
-        } else {
-            s_err = 1;
-        }
-    }
-    __syncthreads();
-
-    for (int t = 0; t < ntiles && !s_err; t++) {
-        if (tid == 0 && t + 1 < ntiles) {
-            if (wait_bar(bar + 1 + (t + 1) % NS, ((t + 1) / NS) & 1)) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                issue_mma(t + 1);
-            } else {
-                s_err = 1;
+    if (warp == EPI_WARPS) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0 && ntiles > 0) {
+            mbar_expect_tx(barA, (uint32_t)a.atoms * a_atom);
+            for (int at = 0; at < a.atoms; at++) tma_load_2d(sA + at * a_atom, &tmA, at * KA, (int)q0, barA);
+            int nl = 0, st = 0;
+            uint32_t ph = 0;
+            for (int t = 0; t < ntiles && !*err; t++) {
+                if (!wait_bar(empty + st, ph ^ 1)) {  // round 0 passes at once
+                    *err = 1;
+                    break;
+                }
+                const int y = (int)(r_begin + (int64_t)t * span);
+                mbar_expect_tx(full + st, b_stage);
+                for (int at = 0; at < a.atoms; at++)
+                    tma_load_2d(sB + st * b_stage + at * b_atom, &tmB, at * KA, y, full + st);
+                nl = t + 1;
+                if (++st == ns) {
+                    st = 0;
+                    ph ^= 1;
+                }
             }
+            s_nl = nl;
         }
-        if (!wait_bar(mdone + (t & 1), (t >> 1) & 1)) s_err = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!s_err) {
-            const int64_t col0 = r_begin + (int64_t)t * TN;
-            const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((t & 1) * TN);
-            for (int c0 = 0; c0 < TN; c0 += 32) {
-                uint32_t v[32];
-                TMEM_LD32(tbase + c0, v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else if (warp == EPI_WARPS + 1) {
+        // --------------------------------------------------------------- MMA
+        if (lane == 0 && ntiles > 0) {
+            int nc = 0, nm = 0, st = 0;
+            uint32_t ph = 0;
+            if (!wait_bar(barA, 0)) *err = 1;
+            for (int t = 0; t < ntiles && !*err; t++) {
+                const int b = t % NT;
+                if (!wait_bar(full + st, ph)) {
+                    *err = 1;
+                    break;
+                }
+                nc = t + 1;
+                if (!wait_bar(tempty + b, ((t / NT) & 1) ^ 1)) {
+                    *err = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint8_t *bs = sB + st * b_stage;
+                const uint32_t d = tmem + (uint32_t)(b * TN);
+                for (int at = 0; at < a.atoms; at++)
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int64_t col = col0 + c0 + j;
-                    if (col >= r_end) continue;
-                    const float s = __uint_as_float(v[j]);
-                    const float dist = a.metric == SVF_IP ? -s : fmaf(-2.f, s, __ldg(a.norms + col));
-                    if (dist < thr) {
-                        int p = KC - 1;
-                        while (p > 0 && ld[(p - 1) * TM + tid] > dist) {
-                            ld[p * TM + tid] = ld[(p - 1) * TM + tid];
-                            li[p * TM + tid] = li[(p - 1) * TM + tid];
-                            p--;
+                    for (int j = 0; j < 2; j++)  // K = 16 per MMA: two per atom
+                        mma_bf16(d, sw64_desc(sA + at * a_atom + j * 32), sw64_desc(bs + at * b_atom + j * 32),
+                                 (at | j) != 0);
+                mma_commit(empty + st);  // the stage may be refilled once these MMAs have read it
+                mma_commit(tfull + b);
+                nm = t + 1;
+                if (++st == ns) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+            s_nc = nc;
+            s_nm = nm;
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        float thr = seed0;  // this query's KC-th best approximate distance so far
+        int cnt = 0;           // pending entries
+        // Merge the pending entries into the sorted list.  All lanes of a
+        // warp merge together (each its own query), so the insertions run
+        // side by side instead of one lane at a time; rows past the slice
+        // end (zero fill of the last tile) are dropped here.
+        auto flush = [&]() {
+            for (int e = 0; e < cnt; e++) {
+                const float2 c = pend[e * TM];
+                const uint32_t col = __float_as_uint(c.y);
+                if (c.x < thr && (int64_t)col < r_end) {
+                    int p = KC - 1;
+                    while (p > 0 && lst_d[(p - 1) * TM] > c.x) {
+                        lst_d[p * TM] = lst_d[(p - 1) * TM];
+                        lst_i[p * TM] = lst_i[(p - 1) * TM];
+                        p--;
+                    }
+                    lst_d[p * TM] = c.x;
+                    lst_i[p * TM] = col;
+                    thr = lst_d[(KC - 1) * TM];
+                }
+            }
+            cnt = 0;
+        };
+        for (int t = 0; t < ntiles; t++) {
+            const int b = t % NT;
+            const bool got = wait_bar(tfull + b, (t / NT) & 1);
+            if (__any_sync(kFull, !got || *err)) {  // warp-uniform exit
+                if (lane == 0) *err = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            constexpr int NC = TN / HALVES;         // columns of this warp
+            constexpr int NG = NC < 64 ? NC : 64;  // columns read from TMEM at a time
+            const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * TN + half * NC);
+            const int64_t col0 = r_begin + (int64_t)t * span + half * NC;
+#pragma unroll 1
+            for (int g = 0; g < NC; g += NG) {
+                uint32_t v[NG];
+#pragma unroll
+                for (int c = 0; c < NG; c += 32) TMEM_LD32(tbase + g + c, (v + c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (g + NG == NC) {  // all of this warp's columns are in registers: free the buffer
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty + b);
+                }
+#pragma unroll
+                for (int c0 = 0; c0 < NG; c0 += 32) {
+                    const uint32_t cb = (uint32_t)(col0 + g + c0);
+                    if (a.metric != SVF_IP) {
+                        // L2 without ||q||^2: lane j holds the norm of column j
+                        const float nrm = __ldg(a.norms + min((int64_t)cb + lane, a.n - 1));
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            v[c0 + j] =
+                                __float_as_uint(fmaf(-2.f, __uint_as_float(v[c0 + j]), __shfl_sync(kFull, nrm, j)));
+                    }
+                    // smallest approximate distance of the 32 columns; the
+                    // append path runs only when some lane of the warp beats
+                    // its threshold
+                    const float dmin = a.metric == SVF_IP ? -max32(v + c0) : -max32_neg(v + c0);
+                    if (__any_sync(kFull, dmin < thr)) {
+#pragma unroll
+                        for (int h16 = 0; h16 < 32; h16 += BUF) {
+#pragma unroll
+                            for (int j = h16; j < h16 + BUF; j++) {
+                                const float dist =
+                                    a.metric == SVF_IP ? -__uint_as_float(v[c0 + j]) : __uint_as_float(v[c0 + j]);
+                                if (dist < thr) pend[(cnt++) * TM] = make_float2(dist, __uint_as_float(cb + j));
+                            }
+                            flush();
                         }
-                        ld[p * TM + tid] = dist;
-                        li[p * TM + tid] = (uint32_t)col;
-                        thr = ld[(KC - 1) * TM + tid];
                     }
                 }
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && t + NS < ntiles && !s_err) load_b(t + NS);  // stage t % NS is free: MMA t has completed
+
     }
-    if (s_err && tid == 0) set_error(a.status, SVF_ETIMEOUT, blockIdx.x);
-    const int64_t q = q0 + tid;
-    if (q < a.nq) {
-        float *od = a.cand_d + (q * a.splits + blockIdx.y) * KC;
-        uint32_t *oi = a.cand_i + (q * a.splits + blockIdx.y) * KC;
+    __syncthreads();
+    if (s_err && tid == 0) {
+        // drain: copies and MMAs still in flight land before TMEM is freed
+        if (ntiles > 0) wait_bar(barA, 0);
+        for (int t = s_nc; t < s_nl; t++) wait_bar(full + t % ns, (t / ns) & 1);
+        if (s_nm > 0) wait_bar(tfull + (s_nm - 1) % NT, ((s_nm - 1) / NT) & 1);  // commits track all earlier MMAs
+        set_error(a.status, SVF_ETIMEOUT, blockIdx.x);
+    }
+    const int64_t q = q0 + qr;
+    if (warp < EPI_WARPS && q < a.nq) {
+        const int64_t o = ((q * a.splits + blockIdx.y) * HALVES + half) * KC;
         for (int j = 0; j < KC; j++) {
-            od[j] = ld[j * TM + tid];
-            oi[j] = li[j * TM + tid];
+            a.cand_d[o + j] = lst_d[j * TM];
+            a.cand_i[o + j] = lst_i[j * TM];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -226,15 +386,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// fp32 rows -> bf16 rows padded to KP columns (+ squared norms).
-__global__ void to_bf16_kernel(const float *X, int64_t n, int d, __nv_bfloat16 *out, float *norms) {
+// fp32 rows -> bf16 rows padded to kp columns (+ squared norms).
+__global__ void to_bf16_kernel(const float *X, int64_t n, int d, int kp, __nv_bfloat16 *out, float *norms) {
     const int lane = threadIdx.x & 31;
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= n) return;
     float ss = 0.f;
-    for (int c = lane; c < KP; c += 32) {
+    for (int c = lane; c < kp; c += 32) {
         const float v = c < d ? X[r * d + c] : 0.f;
-        out[r * KP + c] = __float2bfloat16_rn(v);
+        out[r * kp + c] = __float2bfloat16_rn(v);
         ss = fmaf(v, v, ss);
     }
 #pragma unroll
@@ -251,24 +411,49 @@ __global__ void max_kernel(const float *v, int64_t n, unsigned int *out) {
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as uints
 }
 
+// Seed of a query: the r-th smallest approximate distance in the union of
+// its sorted lists from the strided sample pass (r rounds of taking the
+// smallest list head).
+__global__ void seed_kernel(const float *cand_d, int64_t nq, int lists, int r, float *seed) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const float *l = cand_d + q * lists * KC;
+    uint8_t head[64 * HALVES];
+    for (int i = 0; i < lists; i++) head[i] = 0;
+    float v = INFINITY;
+    for (int m = 0; m < r; m++) {
+        int best = -1;
+        float bv = INFINITY;
+        for (int i = 0; i < lists; i++)
+            if (head[i] < KC && l[i * KC + head[i]] < bv) {
+                bv = l[i * KC + head[i]];
+                best = i;
+            }
+        if (best < 0) break;
+        v = bv;
+        head[best]++;
+    }
+    seed[q] = v;
+}
+
 // Warp per query: exact fp32 distances of all candidates, best k by
 // (distance, id), and the certificate (flag = 1 when it fails).
 __global__ void rescore_kernel(const float *X, const float *Q, int d, int metric, const float *norms,
-                               const unsigned int *maxnorm2, int splits, const float *cand_d, const uint32_t *cand_i,
+                               const unsigned int *maxnorm2, int lists, const float *cand_d, const uint32_t *cand_i,
                                int64_t nq, int k, uint64_t *out_keys, int32_t *flagged, unsigned long long *nflag) {
     extern __shared__ uint64_t rk[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (q >= nq) return;
-    const int nc = splits * KC;
+    const int nc = lists * KC;
     uint64_t *keys = rk + (size_t)wib * nc;
     const float *qr = Q + q * d;
     float qn = 0.f;
     for (int c = lane; c < d; c += 32) qn = fmaf(qr[c], qr[c], qn);
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) qn += __shfl_xor_sync(kFull, qn, m);
-    float bound = INFINITY;  // smallest per-slice 48th approximate distance
-    for (int s = 0; s < splits; s++) bound = fminf(bound, cand_d[(q * splits + s) * KC + KC - 1]);
+    float bound = INFINITY;  // smallest KC-th approximate distance over the lists
+    for (int s = 0; s < lists; s++) bound = fminf(bound, cand_d[(q * lists + s) * KC + KC - 1]);
     for (int e = lane; e < nc; e += 32) {
         const uint32_t id = cand_i[q * nc + e];
         if (id == kEmpty) {
@@ -342,29 +527,42 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *m, void *base, int64_t rows, int box_rows) {
+bool make_map(CUtensorMap *m, void *base, int64_t rows, int kp, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)KP, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)KP * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {KA, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+              CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
 }
 
+// Database slices per query tile: one CTA per SM, so the grid (query
+// tiles x slices) should fill whole waves of the 148 SMs.  Take the
+// smallest count that fills at least one wave with >= 95% of the last
+// wave busy, else the best fill up to 64 slices.
 int split_count(int64_t n, int64_t nq) {
+    constexpr int kSMs = 148;
     const int64_t qt = (nq + TM - 1) / TM;
-    int64_t s = (4 * 148 + qt - 1) / qt;
-    const int64_t max_s = (n + TN - 1) / TN;
-    if (s > max_s) s = max_s;
-    if (s > 64) s = 64;
-    return (int)(s < 1 ? 1 : s);
+    const int64_t max_s = std::min<int64_t>(64, (n + TN - 1) / TN);
+    int64_t best = 1;
+    double best_eff = 0.0;
+    for (int64_t s = 1; s <= max_s; s++) {
+        const int64_t ctas = qt * s;
+        const double eff = (double)ctas / (double)(kSMs * ((ctas + kSMs - 1) / kSMs));
+        if (ctas >= kSMs && eff >= 0.95) return (int)s;
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = s;
+        }
+    }
+    return (int)best;
 }
 
 struct TcLayout {
-    size_t xb, qb, norms, maxn, cd, ci, keys, flagged, nflag, gq, gk, total;
+    size_t xb, qb, norms, maxn, cd, ci, keys, flagged, nflag, gq, gk, seed, total;
 };
 
 TcLayout tc_layout(int64_t n, int64_t nq, int k, int d) {
@@ -376,17 +574,19 @@ TcLayout tc_layout(int64_t n, int64_t nq, int k, int d) {
         o += align256(bytes);
         return at;
     };
-    L.xb = take((size_t)n * KP * 2);
-    L.qb = take((size_t)nq * KP * 2);
+    const int kp = (d + KA - 1) / KA * KA;
+    L.xb = take((size_t)n * kp * 2);
+    L.qb = take((size_t)nq * kp * 2);
     L.norms = take((size_t)n * 4);
     L.maxn = take(256);
-    L.cd = take((size_t)nq * s * KC * 4);
-    L.ci = take((size_t)nq * s * KC * 4);
+    L.cd = take((size_t)nq * s * HALVES * KC * 4);
+    L.ci = take((size_t)nq * s * HALVES * KC * 4);
     L.keys = take((size_t)nq * k * 8);
     L.flagged = take((size_t)nq * 4);
     L.nflag = take(256);
     L.gq = take((size_t)nq * d * 4);
     L.gk = take((size_t)nq * k * 8);
+    L.seed = take((size_t)nq * 4);
     L.total = o;
     return L;
 }
@@ -424,20 +624,20 @@ int svf_knn_tc(const float *X, int64_t n, int32_t d, int32_t metric, const float
     uint64_t *keys = reinterpret_cast<uint64_t *>(S + L.keys);
     int32_t *flagged = reinterpret_cast<int32_t *>(S + L.flagged);
     unsigned long long *nflag = reinterpret_cast<unsigned long long *>(S + L.nflag);
-    to_bf16_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(X, n, d, xb, norms);
-    to_bf16_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(Q, nq, d, qb, nullptr);
+    const int kp = (d + KA - 1) / KA * KA;
+    to_bf16_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(X, n, d, kp, xb, norms);
+    to_bf16_kernel<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(Q, nq, d, kp, qb, nullptr);
     CUDA_TRY(cudaMemsetAsync(maxn, 0, 4, st));
     CUDA_TRY(cudaMemsetAsync(nflag, 0, 8, st));
     max_kernel<<<296, 256, 0, st>>>(norms, n, maxn);
     CUtensorMap ta, tb;
-    if (!make_map(&ta, qb, nq, TM) || !make_map(&tb, xb, n, TN))
+    if (!make_map(&ta, qb, nq, kp, TM) || !make_map(&tb, xb, n, kp, TN))
         return fail(SVF_ECUDA, "cuTensorMapEncodeTiled is unavailable or rejected the layout");
     TcArgs a{};
     a.n = n;
     a.nq = nq;
-    a.splits = split_count(n, nq);
-    a.rows_per_split = ((n + a.splits - 1) / a.splits + TN - 1) / TN * TN;
     a.metric = metric;
+    a.atoms = kp / KA;
     a.norms = norms;
     a.cand_d = cd;
     a.cand_i = ci;
@@ -445,14 +645,36 @@ int svf_knn_tc(const float *X, int64_t n, int32_t d, int32_t metric, const float
     unsigned long long *status = nflag + 8;
     CUDA_TRY(cudaMemsetAsync(status, 0, 8, st));
     a.status = status;
-    CUDA_TRY(cudaFuncSetAttribute(tc_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    dim3 grid((unsigned)((nq + TM - 1) / TM), (unsigned)a.splits);
-    tc_knn_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(ta, tb, a);
+    a.ns = std::min(NS_MAX, (SMEM_LIMIT - smem_fixed(kp)) / stage_bytes(kp));
+    const int smem = smem_fixed(kp) + a.ns * stage_bytes(kp);
+    CUDA_TRY(cudaFuncSetAttribute(tc_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const unsigned qtiles = (unsigned)((nq + TM - 1) / TM);
+    a.splits = split_count(n, nq);
+    a.rows_per_split = ((n + a.splits - 1) / a.splits + TN - 1) / TN * TN;
+    a.tile_stride = 1;
+    if (n >= kSeedMinRows) {
+        // Seed pass: every kSeedStride-th tile, one slice (few, long lists:
+        // an unseeded list pays for its first insertions).  The r-th best of
+        // that sample sits near rank r * kSeedStride of the whole set, a
+        // threshold most rows of the full pass then fail at once.
+        float *seed = reinterpret_cast<float *>(S + L.seed);
+        TcArgs s1 = a;
+        s1.splits = 1;
+        s1.rows_per_split = (n + TN - 1) / TN * TN;
+        s1.tile_stride = kSeedStride;
+        s1.seed = nullptr;
+        tc_knn_kernel<<<dim3(qtiles, 1), THREADS, smem, st>>>(ta, tb, s1);
+        CUDA_TRY(cudaGetLastError());
+        seed_kernel<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(cd, nq, HALVES, kSeedRank, seed);
+        CUDA_TRY(cudaGetLastError());
+        a.seed = seed;
+    }
+    tc_knn_kernel<<<dim3(qtiles, (unsigned)a.splits), THREADS, smem, st>>>(ta, tb, a);
     CUDA_TRY(cudaGetLastError());
     const int wpb = 4;
-    const size_t rsm = (size_t)wpb * a.splits * KC * 8;
+    const size_t rsm = (size_t)wpb * a.splits * HALVES * KC * 8;
     CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    rescore_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, rsm, st>>>(X, Q, d, metric, norms, maxn, a.splits, cd,
+    rescore_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, rsm, st>>>(X, Q, d, metric, norms, maxn, a.splits * HALVES, cd,
                                                                           ci, nq, k, keys, flagged, nflag);
     CUDA_TRY(cudaGetLastError());
     unsigned long long hf[2] = {0, 0};

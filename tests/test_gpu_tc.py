@@ -18,7 +18,9 @@ def svf():
 
 
 @pytest.mark.parametrize("mix,metric,n,nq,k", [("unit96", "ip", 5000, 300, 10), ("tiny", "l2", 7001, 129, 10),
-                                               ("unit96", "ip", 40000, 1000, 32)])
+                                               ("unit96", "ip", 40000, 1000, 32), ("serve128", "l2", 20011, 300, 10),
+                                               # past the seed-pass threshold (2^17 rows), ragged last tile
+                                               ("unit96", "ip", 200003, 300, 10), ("serve128", "l2", 150001, 200, 10)])
 def test_tc_knn_equals_oracle(svf, orc, mix, metric, n, nq, k):
     X = synth.sample(mix, n, 801)
     Q = synth.sample(mix, nq, 802)
