@@ -138,6 +138,18 @@ STOP_POINTS = [(64, 96), (64, 128), (128, 64), (128, 72), (128, 80), (128, 96)]
 STOP_EVERY = 4
 
 
+def exact_knn(svf, X, Q, k, metric):
+    """Ground-truth ids: the tensor-core scan (bf16 products, exact fp32
+    rescoring, certificate with SIMT fallback) where it applies, else the
+    SIMT scan."""
+    if X.dtype.is_floating_point and X.shape[1] % 16 == 0 and X.shape[1] <= 128 and k <= 32:
+        ids, _, fb = svf.knn_tc(X, Q, k, metric)
+        if fb:
+            print(f"  ground truth: {fb} of {Q.shape[0]} queries by the SIMT fallback", file=sys.stderr, flush=True)
+        return ids
+    return svf.knn(X, Q, k, metric)[0]
+
+
 def train_stops(torch, svf, ix, Qtr, gt_cal, ncal, precisions):
     """One stop network per (precision, L, T_max), trained on traces of the
     plain search of the training queries and calibrated (tau) on held-out
@@ -344,7 +356,7 @@ def serve_main(a, svf, torch, log_t):
     torch.cuda.synchronize()
     log_t("built")
     Qe = torch.from_numpy(synth.sample_chunked("serve128", 2000, 502)).cuda()
-    gt, _ = svf.knn(ix.vectors()[:n], Qe, K, "l2")
+    gt = exact_knn(svf, ix.vectors()[:n], Qe, K, "l2")
     from paper_2601_08528_b300.learned import recall_at_k
     op = None
     for L, T in [(64, 64), (64, 96), (128, 64), (128, 96), (256, 128), (256, 192)]:
@@ -408,7 +420,7 @@ def main():
     ix = build_index(svf, torch, X, log_t)
     Xd = ix.vectors()[:a.n]
     Qe = torch.from_numpy(Qe_np).cuda()
-    gt, _ = svf.knn(Xd, Qe, K, "ip")
+    gt = exact_knn(svf, Xd, Qe, K, "ip")
     torch.cuda.synchronize()
     log_t("ground truth")
 
@@ -441,7 +453,7 @@ def main():
     # learned stop: traces of the plain search of training queries
     Qtr = torch.from_numpy(synth.sample_chunked("unit96", a.ntrain, 401)).cuda()
     ncal = a.ntrain // 10
-    gt_cal, _ = svf.knn(Xd, Qtr[:ncal], K, "ip")
+    gt_cal = exact_knn(svf, Xd, Qtr[:ncal], K, "ip")
     nets = train_stops(torch, svf, ix, Qtr, gt_cal, ncal, ["bf16", "fp8"])
     del Qtr
     log_t("stop networks")

@@ -29,6 +29,10 @@ namespace svf {
 // Stop-network inference (16 -> 64 relu -> 1) reads the packed bf16 layout
 // of mlp.cu: W1 [64][16], b1 [64], w2 [64], b2.
 
+// Up to this many admitted candidates are inserted one at a time (rank by
+// ballot, shift by shuffle); more are sorted and merged.
+constexpr int kFastInsert = 8;
+
 __device__ __forceinline__ uint32_t hash_slot(uint32_t id, int bits) { return (id * 0x9E3779B1u) >> (32 - bits); }
 
 // Insert id; true if it was not present.  The table is kept at most half
@@ -82,7 +86,9 @@ __device__ __forceinline__ float pool_dist(const uint64_t (&pool)[LW], int e, in
     return dtype == SVF_U8 ? (float)(int32_t)v : __uint_as_float(v);
 }
 
-template <int DT, int R, int LW, bool LEARN>
+// NCH > 0: the traversal rows are NCH 16-byte chunks (the launcher checks
+// the store against it); 0: any layout, read from a.trav at run time.
+template <int DT, int R, int LW, bool LEARN, int NCH>
 __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_kernel(const SearchArgs a) {
     constexpr int L = 32 * LW;
     constexpr int S = R / 32;  // graph ids per lane
@@ -146,7 +152,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
     int hcount = np;
     const TierCtx *tier = a.trav.map ? &a.tier : nullptr;
     int hits = 0, misses = 0;
-    if (!staged_dist<DT>(stg, a.trav, list, np, keys, 0u, lane, qf, qb, tier, &hits, &misses)) {
+    if (!staged_dist<DT, NCH>(stg, a.trav, list, np, keys, 0u, lane, qf, qb, tier, &hits, &misses)) {
         if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
         return;
     }
@@ -162,9 +168,6 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
     constexpr bool learn = LEARN;
     FeatState fs{0.f, 1.f, 0.f, -1};
     float inv_s0 = 1.f, inv_T = 1.f, inv_k = 1.f;
-    // this lane's share of the stop network: hidden units lane and lane+32
-    uint32_t w1p[2][8] = {}, hb[2] = {};
-    float b2 = 0.f;
     if (learn) {
         float d1 = pool_dist<LW>(pool, 0, a.out_dtype, a.trav.metric);
         float dl = pool_dist<LW>(pool, max(np - 1, 0), a.out_dtype, a.trav.metric);
@@ -173,18 +176,6 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         inv_s0 = 1.f / fs.s0;
         inv_T = 1.f / (float)max(a.T, 1);
         inv_k = 1.f / (float)a.k;
-        if (a.mlp) {
-            const uint32_t *wp = reinterpret_cast<const uint32_t *>(a.mlp);  // bf16 pairs
-            const uint16_t *wh = reinterpret_cast<const uint16_t *>(a.mlp);
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int j = lane + 32 * h;
-#pragma unroll
-                for (int i = 0; i < 8; i++) w1p[h][i] = __ldg(wp + j * 8 + i);
-                hb[h] = (uint32_t)__ldg(wh + kMlpOffB1 + j) | ((uint32_t)__ldg(wh + kMlpOffW2 + j) << 16);
-            }
-            b2 = __uint_as_float((uint32_t)__ldg(wh + kMlpOffB2) << 16);
-        }
     }
 
     int iters = 0, evals = np, resets = 0, ran = 0;
@@ -248,7 +239,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         }
         evals += nf - ndel;
         const uint32_t newflag = learn ? kNewBit : 0u;
-        if (!staged_dist<DT>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb, tier, &hits, &misses)) {
+        if (!staged_dist<DT, NCH>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb, tier, &hits, &misses)) {
             if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
             return;
         }
@@ -276,7 +267,18 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
             nin += __popc(__ballot_sync(kFull, !key_is_pad(cand[s])));
         }
         nf -= ndel;
-        if (nin > 0) {
+        if (nin > 0 && nin <= kFastInsert) {
+            // most iterations admit a few candidates: insert them one by one
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                uint32_t m = __ballot_sync(kFull, !key_is_pad(cand[s]));
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    warp_insert_one<LW>(pool, shfl64(cand[s], src), lane);
+                }
+            }
+        } else if (nin > 0) {
             warp_sort<S>(cand, lane);
             if constexpr (S <= LW) {
                 warp_merge_into<LW, S>(pool, cand, lane);
@@ -360,21 +362,27 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
                 a.trace_feat[(qi * a.T + t) * 16 + lane] = fv;
             }
             if (evalz) {
-                // lane j computes hidden units j and j+32 from its registers
+                // lane j computes hidden units j and j+32; the packed bf16
+                // weights are read through L1 (2.3 KB shared by all warps)
+                const uint4 *wp = reinterpret_cast<const uint4 *>(a.mlp);  // W1 rows: 16 bf16 = 2 x uint4
+                const uint16_t *wh = reinterpret_cast<const uint16_t *>(a.mlp);
                 float z = 0.f;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    float acc = __uint_as_float(hb[h] << 16);
+                    const int j = lane + 32 * h;
+                    const uint4 r0 = __ldg(wp + 2 * j), r1 = __ldg(wp + 2 * j + 1);
+                    const uint32_t w[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                    float acc = __uint_as_float((uint32_t)__ldg(wh + kMlpOffB1 + j) << 16);
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
-                        acc = fmaf(__uint_as_float(w1p[h][i] << 16), f[2 * i], acc);
-                        acc = fmaf(__uint_as_float(w1p[h][i] & 0xFFFF0000u), f[2 * i + 1], acc);
+                        acc = fmaf(__uint_as_float(w[i] << 16), f[2 * i], acc);
+                        acc = fmaf(__uint_as_float(w[i] & 0xFFFF0000u), f[2 * i + 1], acc);
                     }
-                    if (acc > 0.f) z = fmaf(__uint_as_float(hb[h] & 0xFFFF0000u), acc, z);
+                    if (acc > 0.f) z = fmaf(__uint_as_float((uint32_t)__ldg(wh + kMlpOffW2 + j) << 16), acc, z);
                 }
 #pragma unroll
                 for (int m = 16; m > 0; m >>= 1) z += __shfl_xor_sync(kFull, z, m);
-                z += b2;
+                z += __uint_as_float((uint32_t)__ldg(wh + kMlpOffB2) << 16);
                 if (z >= a.z_tau) break;
             }
         }
@@ -434,6 +442,59 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
             atomicAdd(a.status + kStMisses, (unsigned long long)misses);
         }
     }
+}
+
+// Launch search_kernel<DT, R, LW, LEARN, NCH> for a pool of 32 * LW.
+template <int DT, int R, bool LEARN, int NCH>
+cudaError_t launch_search_lw(const SearchArgs &a, int LW, size_t smem, cudaStream_t st) {
+    const dim3 grid((unsigned)((a.nq + kSearchWarps - 1) / kSearchWarps)), block(kSearchWarps * 32);
+    auto go = [&](auto kernel) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return cudaGetLastError();
+        kernel<<<grid, block, smem, st>>>(a);
+        return cudaGetLastError();
+    };
+    switch (LW) {
+    case 1: return go(search_kernel<DT, R, 1, LEARN, NCH>);
+    case 2: return go(search_kernel<DT, R, 2, LEARN, NCH>);
+    case 4: return go(search_kernel<DT, R, 4, LEARN, NCH>);
+    case 8: return go(search_kernel<DT, R, 8, LEARN, NCH>);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The compile-time row layouts of a dtype: d = 96 and d = 128.
+template <int DT>
+constexpr int nch_for_dim(int d) {
+    return d * (DT == SVF_F32 ? 4 : DT == SVF_BF16 ? 2 : 1) / 16;
+}
+template <int DT, int NCH>
+bool layout_is(const RowDesc &r) {
+    return r.nchunk == NCH && r.copy_bytes == staged_row_bytes<DT, NCH>() && r.ts == team_for(NCH) &&
+           r.cpl == (NCH + team_for(NCH) - 1) / team_for(NCH);
+}
+
+// Dispatch on R, learned features and the row layout (specialised for the
+// out-degree `RS` at d = 96 and d = 128; everything else takes the generic
+// kernel).
+template <int DT, int RS>
+cudaError_t launch_search_dtype(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st) {
+    constexpr int N96 = nch_for_dim<DT>(96), N128 = nch_for_dim<DT>(128);
+    if (R == RS) {
+        if (layout_is<DT, N96>(a.trav))
+            return learn ? launch_search_lw<DT, RS, true, N96>(a, LW, smem, st)
+                         : launch_search_lw<DT, RS, false, N96>(a, LW, smem, st);
+        if (layout_is<DT, N128>(a.trav))
+            return learn ? launch_search_lw<DT, RS, true, N128>(a, LW, smem, st)
+                         : launch_search_lw<DT, RS, false, N128>(a, LW, smem, st);
+    }
+    if (R == 32)
+        return learn ? launch_search_lw<DT, 32, true, 0>(a, LW, smem, st)
+                     : launch_search_lw<DT, 32, false, 0>(a, LW, smem, st);
+    if (R == 64)
+        return learn ? launch_search_lw<DT, 64, true, 0>(a, LW, smem, st)
+                     : launch_search_lw<DT, 64, false, 0>(a, LW, smem, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace svf

@@ -141,6 +141,30 @@ __device__ __forceinline__ void warp_merge_into(uint64_t (&pool)[LW], const uint
     warp_bitonic_merge<LW>(pool, lane);
 }
 
+// pool (32*LW, sorted) <- the 32*LW smallest of pool and {c}: c's rank is
+// counted by ballots, entries from that rank on move up one place (the
+// last one leaves) and c takes the freed slot.  Keys are distinct, so a
+// sequence of these gives the same pool as sorting and merging the set.
+template <int LW>
+__device__ __forceinline__ void warp_insert_one(uint64_t (&pool)[LW], uint64_t c, int lane) {
+    const uint64_t cc = cmpk(c);
+    int r = 0;
+#pragma unroll
+    for (int s = 0; s < LW; s++) r += __popc(__ballot_sync(kFull, cmpk(pool[s]) < cc));
+    if (r >= 32 * LW) return;
+#pragma unroll
+    for (int s = LW - 1; s >= 0; s--) {  // downwards: pool[s - 1] is still the old row here
+        uint32_t lo = __shfl_up_sync(kFull, (uint32_t)pool[s], 1), hi = __shfl_up_sync(kFull, (uint32_t)(pool[s] >> 32), 1);
+        uint64_t up = ((uint64_t)hi << 32) | lo;
+        if (s > 0) {
+            const uint64_t last = shfl64(pool[s - 1], 31);
+            if (lane == 0) up = last;
+        }
+        const int e = s * 32 + lane;
+        if (e >= r) pool[s] = e == r ? c : up;
+    }
+}
+
 // ---------------------------------------------------------------- distances
 // A row is split into 16-byte chunks; the 8 lanes of a team take chunks
 // sub, sub+8, sub+16, ... and the partial sums are combined by xor shuffles
@@ -188,6 +212,36 @@ __device__ __forceinline__ float4 bf2_to_f4(uint32_t a, uint32_t b) {
     return make_float4(__uint_as_float(a << 16), __uint_as_float(a & 0xFFFF0000u), __uint_as_float(b << 16),
                        __uint_as_float(b & 0xFFFF0000u));
 }
+// Packed fp32 pairs (Blackwell f32x2 instructions): each half is an
+// independent IEEE fp32 lane, rounded as the scalar instruction would be.
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float f2sum(uint64_t p) {
+    return __uint_as_float((uint32_t)p) + __uint_as_float((uint32_t)(p >> 32));
+}
+// a.xy . b.xy + a.zw . b.zw into the two packed accumulators (IP), or
+// (a - s b)^2 summed likewise (L2; s = 1 for bf16)
+__device__ __forceinline__ void dot4_2(float4 q, float2 x01, float2 x23, uint64_t (&p)[2]) {
+    p[0] = ffma2(f2pack(q.x, q.y), f2pack(x01.x, x01.y), p[0]);
+    p[1] = ffma2(f2pack(q.z, q.w), f2pack(x23.x, x23.y), p[1]);
+}
+__device__ __forceinline__ void l2_4_2(float4 q, float2 x01, float2 x23, uint64_t nscale2, uint64_t (&p)[2]) {
+    const uint64_t d0 = ffma2(f2pack(x01.x, x01.y), nscale2, f2pack(q.x, q.y));  // q - s x, one rounding
+    const uint64_t d1 = ffma2(f2pack(x23.x, x23.y), nscale2, f2pack(q.z, q.w));
+    p[0] = ffma2(d0, d0, p[0]);
+    p[1] = ffma2(d1, d1, p[1]);
+}
+__device__ __forceinline__ float2 fp8x2_to_f2(uint32_t w16) {
+    __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w16 & 0xFFFFu), __NV_E4M3);
+    return __half22float2(*reinterpret_cast<__half2 *>(&h));
+}
+
 __device__ __forceinline__ float4 fp8x4_to_f4(uint32_t w) {
     __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
     __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
@@ -202,7 +256,7 @@ __device__ __forceinline__ float4 fp8x4_to_f4(uint32_t w) {
 // applies it per element.
 template <int DT>
 __device__ __forceinline__ void chunk_acc(int metric, const uint4 v, int c, const float *qf, const uint8_t *qb,
-                                          float scale, float &facc, uint32_t &iacc) {
+                                          float scale, float &facc, uint32_t &iacc, uint64_t (&pacc)[2]) {
     if constexpr (DT == SVF_F32) {
         float4 x = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
                                __uint_as_float(v.w));
@@ -224,29 +278,39 @@ __device__ __forceinline__ void chunk_acc(int metric, const uint4 v, int c, cons
             iacc = __dp4a(v.w, q.w, iacc);
         }
     } else if constexpr (DT == SVF_BF16) {
+        // packed pairs, two accumulators (four fp32 partial sums per lane)
         const float4 *q = reinterpret_cast<const float4 *>(qf) + 2 * c;
-        float4 x0 = bf2_to_f4(v.x, v.y), x1 = bf2_to_f4(v.z, v.w);
-        if (metric == SVF_L2) {
-            facc = l2_4(q[0], x0, facc);
-            facc = l2_4(q[1], x1, facc);
-        } else {
-            facc = dot4(q[0], x0, facc);
-            facc = dot4(q[1], x1, facc);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        const uint64_t m1 = f2pack(-1.f, -1.f);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const float2 x01 = make_float2(__uint_as_float(w[2 * h] << 16), __uint_as_float(w[2 * h] & 0xFFFF0000u));
+            const float2 x23 =
+                make_float2(__uint_as_float(w[2 * h + 1] << 16), __uint_as_float(w[2 * h + 1] & 0xFFFF0000u));
+            if (metric == SVF_L2)
+                l2_4_2(q[h], x01, x23, m1, pacc);
+            else
+                dot4_2(q[h], x01, x23, pacc);
         }
-    } else {  // FP8
+    } else {  // FP8: codes; IP scales after the sum, L2 scales each code
         const float4 *q = reinterpret_cast<const float4 *>(qf) + 4 * c;
-        float4 x[4] = {fp8x4_to_f4(v.x), fp8x4_to_f4(v.y), fp8x4_to_f4(v.z), fp8x4_to_f4(v.w)};
-        if (metric == SVF_L2) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        const uint64_t ns2 = f2pack(-scale, -scale);
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                float4 xs = make_float4(x[u].x * scale, x[u].y * scale, x[u].z * scale, x[u].w * scale);
-                facc = l2_4(q[u], xs, facc);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; u++) facc = dot4(q[u], x[u], facc);
+        for (int u = 0; u < 4; u++) {
+            const float2 x01 = fp8x2_to_f2(w[u]), x23 = fp8x2_to_f2(w[u] >> 16);
+            if (metric == SVF_L2)
+                l2_4_2(q[u], x01, x23, ns2, pacc);
+            else
+                dot4_2(q[u], x01, x23, pacc);
         }
     }
+}
+
+// fold the packed partial sums of a low-precision row into facc
+template <int DT>
+__device__ __forceinline__ void fold_pacc(float &facc, const uint64_t (&pacc)[2]) {
+    if constexpr (DT == SVF_BF16 || DT == SVF_FP8) facc = f2sum(pacc[0]) + f2sum(pacc[1]);
 }
 
 template <int DT>
@@ -271,6 +335,7 @@ __device__ __forceinline__ void team_dist_key2(const RowDesc &R, uint32_t ida, b
                                                uint32_t &kb) {
     float fa = 0.0f, fb = 0.0f, sa = 1.0f, sb = 1.0f;
     uint32_t ia = 0, ib = 0;
+    uint64_t pa[2] = {0, 0}, pb[2] = {0, 0};
     const uint8_t *ra = row_ptr(R, ida);
     const uint8_t *rb = row_ptr(R, idb);
     if (DT == SVF_FP8) {
@@ -288,10 +353,12 @@ __device__ __forceinline__ void team_dist_key2(const RowDesc &R, uint32_t ida, b
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             int c = c0 + u * kTeam;
-            if (va && c < R.nchunk) chunk_acc<DT>(R.metric, a[u], c, qf, qb, sa, fa, ia);
-            if (vb && c < R.nchunk) chunk_acc<DT>(R.metric, b[u], c, qf, qb, sb, fb, ib);
+            if (va && c < R.nchunk) chunk_acc<DT>(R.metric, a[u], c, qf, qb, sa, fa, ia, pa);
+            if (vb && c < R.nchunk) chunk_acc<DT>(R.metric, b[u], c, qf, qb, sb, fb, ib, pb);
         }
     }
+    fold_pacc<DT>(fa, pa);
+    fold_pacc<DT>(fb, pb);
 #pragma unroll
     for (int m = kTeam / 2; m > 0; m >>= 1) {
         if constexpr (DT == SVF_U8) {
@@ -483,25 +550,44 @@ __device__ __forceinline__ void tier_miss(const TierCtx &T, uint32_t id) {
         atomicAnd(T.freq + id, ~kQueuedBit);  // queue full: let a later miss queue it
 }
 
+// Staged-row layout known at compile time (NCH 16-byte value chunks per
+// row): the team size and chunks per lane of set_team, and the staged row
+// bytes (values, plus the scale slot for FP8).
+__host__ __device__ constexpr int team_for(int nch) {
+    int ts = 1;
+    while (ts < 32 && (nch + ts - 1) / ts > 4) ts <<= 1;
+    return ts;
+}
+template <int DT, int NCH>
+__host__ __device__ constexpr int staged_row_bytes() {
+    return NCH * 16 + (DT == SVF_FP8 ? 16 : 0);
+}
+
 // Distance keys of rows list[0..n) (smem ids) written to keys[0..n) with
 // `flags` or'ed into the id word.  Rows are staged in chunks that fit the
 // buffer; each chunk is one batch of bulk copies and one barrier wait.
 // Returns false if a wait gave up (the caller reports SVF_ETIMEOUT).
-template <int DT>
+// NCH > 0: the row layout is NCH chunks (the caller has checked R against
+// it), so loop bounds and predicates fold at compile time.
+template <int DT, int NCH = 0>
 __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const uint32_t *list, int n, uint64_t *keys,
                                             uint32_t flags, int lane, const float *qf, const uint8_t *qb,
                                             const TierCtx *tier = nullptr, int *hits = nullptr, int *misses = nullptr) {
-    const int per = (int)(S.cap / (uint32_t)R.copy_bytes);
-    const int ts = R.ts, team = lane / ts, sub = lane % ts, nteam = 32 / ts;
+    constexpr bool CT = NCH > 0;
+    const int cb = CT ? staged_row_bytes<DT, NCH>() : R.copy_bytes;
+    const int nch = CT ? NCH : R.nchunk;
+    const int cpl = CT ? (NCH + team_for(NCH) - 1) / team_for(NCH) : R.cpl;
+    const int per = (int)(S.cap / (uint32_t)cb);
+    const int ts = CT ? team_for(NCH) : R.ts, team = lane / ts, sub = lane % ts, nteam = 32 / ts;
     for (int i0 = 0; i0 < n; i0 += per) {
         const int cnt = min(per, n - i0);
         __syncwarp();
         fence_proxy_async();  // earlier reads of the buffer precede the new async writes
         if (!R.map) {
-            if (lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(cnt * R.copy_bytes));
+            if (lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(cnt * cb));
             __syncwarp();
             for (int j = lane; j < cnt; j += 32)
-                bulk_g2s(S.buf + (size_t)j * R.copy_bytes, R.base + (int64_t)list[i0 + j] * R.pitch, R.copy_bytes,
+                bulk_g2s(S.buf + (size_t)j * cb, R.base + (int64_t)list[i0 + j] * R.pitch, cb,
                          S.mbar);
             uint32_t it = 0;
             while (!mbar_try_wait(S.mbar, S.phase))
@@ -514,14 +600,14 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
             for (int j = lane; j < cnt; j += 32) nhit += __ldg(R.map + list[i0 + j]) >= 0;
 #pragma unroll
             for (int m = 16; m > 0; m >>= 1) nhit += __shfl_xor_sync(kFull, nhit, m);
-            if (nhit > 0 && lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(nhit * R.copy_bytes));
+            if (nhit > 0 && lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(nhit * cb));
             __syncwarp();
             uint32_t mmask = 0;  // this lane's missed rows (j = lane + 32 t)
             for (int j = lane, t = 0; j < cnt; j += 32, t++) {
                 const uint32_t id = list[i0 + j];
                 const int32_t slot = __ldg(R.map + id);
                 if (slot >= 0) {
-                    bulk_g2s(S.buf + (size_t)j * R.copy_bytes, R.base + (int64_t)slot * R.pitch, R.copy_bytes, S.mbar);
+                    bulk_g2s(S.buf + (size_t)j * cb, R.base + (int64_t)slot * R.pitch, cb, S.mbar);
                     tier->ref[slot] = 1;
                 } else {
                     mmask |= 1u << t;
@@ -530,7 +616,7 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
             }
             // missed rows: the whole warp copies them from host memory, every
             // 16-byte chunk of every missed row spread over the lanes
-            const int cpr = R.copy_bytes / 16;
+            const int cpr = cb / 16;
             for (int j0 = 0; j0 < cnt; j0 += 32) {
                 const uint32_t miss = __ballot_sync(kFull, (mmask >> (j0 >> 5)) & 1u);
                 const int nm = __popc(miss);
@@ -539,7 +625,7 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
                     const int r = e / cpr, c = e - r * cpr;
                     const int j = j0 + __fns(miss, 0, r + 1);  // position of the r-th missed row
                     const uint4 *src = reinterpret_cast<const uint4 *>(R.host + (int64_t)list[i0 + j] * R.pitch);
-                    reinterpret_cast<uint4 *>(S.buf + (size_t)j * R.copy_bytes)[c] = src[c];
+                    reinterpret_cast<uint4 *>(S.buf + (size_t)j * cb)[c] = src[c];
                 }
             }
             if (hits) *hits += nhit;
@@ -555,23 +641,28 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
         for (int r0 = 0; r0 < cnt; r0 += nteam) {
             const int r = r0 + team;
             const bool valid = r < cnt;
-            const uint8_t *row = S.buf + (size_t)(valid ? r : 0) * R.copy_bytes;
+            const uint8_t *row = S.buf + (size_t)(valid ? r : 0) * cb;
             float facc = 0.f, scale = 1.f;
             uint32_t iacc = 0;
+            uint64_t pacc[2] = {0, 0};
             if (DT == SVF_FP8) scale = *reinterpret_cast<const float *>(row + R.d);
             uint4 v[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int c = sub + u * ts;
-                if (valid && u < R.cpl && c < R.nchunk) v[u] = reinterpret_cast<const uint4 *>(row)[c];
+                if (valid && u < cpl && c < nch) v[u] = reinterpret_cast<const uint4 *>(row)[c];
             }
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int c = sub + u * ts;
-                if (valid && u < R.cpl && c < R.nchunk) chunk_acc<DT>(R.metric, v[u], c, qf, qb, scale, facc, iacc);
+                if (valid && u < cpl && c < nch)
+                    chunk_acc<DT>(R.metric, v[u], c, qf, qb, scale, facc, iacc, pacc);
             }
-            for (int c0 = sub + 4 * ts; c0 < R.nchunk; c0 += ts)  // rows longer than 4 chunks per lane
-                if (valid) chunk_acc<DT>(R.metric, reinterpret_cast<const uint4 *>(row)[c0], c0, qf, qb, scale, facc, iacc);
+            for (int c0 = sub + 4 * ts; c0 < nch; c0 += ts)  // rows longer than 4 chunks per lane
+                if (valid)
+                    chunk_acc<DT>(R.metric, reinterpret_cast<const uint4 *>(row)[c0], c0, qf, qb, scale, facc, iacc,
+                                  pacc);
+            fold_pacc<DT>(facc, pacc);
             for (int m = ts >> 1; m > 0; m >>= 1) {
                 if constexpr (DT == SVF_U8)
                     iacc += __shfl_xor_sync(kFull, iacc, m);
