@@ -107,8 +107,11 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
     stg.buf = reinterpret_cast<uint8_t *>(keys + a.list_len);
     stg.cap = a.stage_bytes;
     stg.mbar = reinterpret_cast<uint64_t *>(stg.buf + a.stage_bytes);
-    stg.phase = 0;
-    if (lane == 0) mbar_init(stg.mbar, 1);
+    stg.phase[0] = stg.phase[1] = 0;
+    if (lane == 0) {
+        mbar_init(stg.mbar, 1);
+        mbar_init(stg.mbar + 1, 1);
+    }
 
     // ---- query to shared memory, query key
     const uint8_t *qsrc = reinterpret_cast<const uint8_t *>(a.Q) + qi * a.q_row_bytes;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         int ps = -1, pl = 0;
 #pragma unroll
         for (int s = 0; s < LW; s++) {
-            uint32_t b = __ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0);
+            const uint32_t b = __ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0);
             if (ps < 0 && b) {
                 ps = s;
                 pl = __ffs(b) - 1;
@@ -229,20 +232,26 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         }
         hcount += nf;
         __syncwarp();
-        bool dflag[S];
-        int ndel = 0;
+        uint32_t dword[S];  // deletion-bitset words, consumed after the rows arrive
 #pragma unroll
         for (int s = 0; s < S; s++) {
             const int e = s * 32 + lane;
-            dflag[s] = e < nf && is_deleted(a.del, list[e]);
-            ndel += __popc(__ballot_sync(kFull, dflag[s]));
+            dword[s] = e < nf ? __ldg(a.del + (list[e] >> 5)) : 0u;
         }
-        evals += nf - ndel;
         const uint32_t newflag = learn ? kNewBit : 0u;
         if (!staged_dist<DT, NCH>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb, tier, &hits, &misses)) {
             if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
             return;
         }
+        bool dflag[S];
+        int ndel = 0;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            const int e = s * 32 + lane;
+            dflag[s] = e < nf && ((dword[s] >> (list[e] & 31)) & 1u);
+            ndel += __popc(__ballot_sync(kFull, dflag[s]));
+        }
+        evals += nf - ndel;
 
         // learned-stop inputs before the merge (only on iterations whose
         // features are used: traced, or where a stop may be taken)

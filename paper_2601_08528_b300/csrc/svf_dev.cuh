@@ -516,10 +516,10 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 constexpr uint32_t kWaitLimit = 1u << 22;  // bounded wait on an mbarrier (each try_wait may also block briefly)
 
 struct Stage {
-    uint8_t *buf;     // per-warp buffer (16-byte aligned)
-    uint32_t cap;     // bytes
-    uint64_t *mbar;   // per-warp mbarrier
-    uint32_t phase;   // parity of the next phase to wait for
+    uint8_t *buf;       // per-warp buffer (16-byte aligned)
+    uint32_t cap;       // bytes
+    uint64_t *mbar;     // two per-warp mbarriers: first and second half of a batch
+    uint32_t phase[2];  // parity of the next phase to wait for, per barrier
 };
 
 // Workload-aware placement state used on cache misses (SVFusion Sec. 4.3):
@@ -583,16 +583,24 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
         const int cnt = min(per, n - i0);
         __syncwarp();
         fence_proxy_async();  // earlier reads of the buffer precede the new async writes
+        // Rows [0, h) complete on barrier 0 and [h, cnt) on barrier 1 (h a
+        // whole number of team rounds), so the first half's distances are
+        // computed while the second half is still arriving.
+        int h = cnt;
         if (!R.map) {
-            if (lane == 0) mbar_expect_tx(S.mbar, (uint32_t)(cnt * cb));
+            const int rounds = (cnt + nteam - 1) / nteam;
+            if (rounds > 1) h = min(cnt, (rounds + 1) / 2 * nteam);
+            if (lane == 0) {
+                mbar_expect_tx(S.mbar, (uint32_t)(h * cb));
+                if (cnt > h) mbar_expect_tx(S.mbar + 1, (uint32_t)((cnt - h) * cb));
+            }
             __syncwarp();
             for (int j = lane; j < cnt; j += 32)
-                bulk_g2s(S.buf + (size_t)j * cb, R.base + (int64_t)list[i0 + j] * R.pitch, cb,
-                         S.mbar);
+                bulk_g2s(S.buf + (size_t)j * cb, R.base + (int64_t)list[i0 + j] * R.pitch, cb, S.mbar + (j >= h));
             uint32_t it = 0;
-            while (!mbar_try_wait(S.mbar, S.phase))
+            while (!mbar_try_wait(S.mbar, S.phase[0]))
                 if (++it > kWaitLimit) return false;
-            S.phase ^= 1u;
+            S.phase[0] ^= 1u;
         } else {
             // tiered store: cached rows by bulk copy from the device cache,
             // missed rows read from host memory by the lane that owns them
@@ -632,13 +640,19 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
             if (misses) *misses += cnt - nhit;
             if (nhit > 0) {
                 uint32_t it = 0;
-                while (!mbar_try_wait(S.mbar, S.phase))
+                while (!mbar_try_wait(S.mbar, S.phase[0]))
                     if (++it > kWaitLimit) return false;
-                S.phase ^= 1u;
+                S.phase[0] ^= 1u;
             }
             __syncwarp();
         }
         for (int r0 = 0; r0 < cnt; r0 += nteam) {
+            if (r0 == h) {  // the second half
+                uint32_t it = 0;
+                while (!mbar_try_wait(S.mbar + 1, S.phase[1]))
+                    if (++it > kWaitLimit) return false;
+                S.phase[1] ^= 1u;
+            }
             const int r = r0 + team;
             const bool valid = r < cnt;
             const uint8_t *row = S.buf + (size_t)(valid ? r : 0) * cb;
