@@ -138,6 +138,10 @@ STOP_POINTS = [(64, 96), (64, 128), (128, 64), (128, 72), (128, 80), (128, 96)]
 STOP_EVERY = 4
 
 
+def unit96_name(n):
+    return f"unit96-{n // 1_000_000}M" if n % 1_000_000 == 0 else f"unit96-{n}"
+
+
 def exact_knn(svf, X, Q, k, metric):
     """Ground-truth ids: the tensor-core scan (bf16 products, exact fp32
     rescoring, certificate with SIMT fallback) where it applies, else the
@@ -443,7 +447,7 @@ def main():
         out = {"impl": "reference", "metric": "search QPS at recall@10>=0.95", "value": v, "unit": "queries/s",
                "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": "unit96-10M", "n": a.n, "d": 96, "R": R, "nq": a.nq, "k": K, "L": op["L"],
+               "config": {"workload": unit96_name(a.n), "n": a.n, "d": 96, "R": R, "nq": a.nq, "k": K, "L": op["L"],
                           "T": op["T"], "form": "fp32", "l2": "inputs larger than L2"},
                "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
                "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -536,9 +540,9 @@ def main():
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": form.split("+")[0],
         "data": "synthetic",
-        "config": {"workload": "unit96-10M", "n": a.n, "d": 96, "R": R, "nq": nq, "k": K, "form": form,
+        "config": {"workload": unit96_name(a.n), "n": a.n, "d": 96, "R": R, "nq": nq, "k": K, "form": form,
                    "L": cfg.L, "T": cfg.T, "tau": getattr(cfg, "tau", None) if cfg.mlp is not None else None,
-                   "recall@10": win["recall"], "l2": "inputs larger than L2 (3.8 GB store, 1.3 GB graph)",
+                   "recall@10": win["recall"], "l2": f"inputs larger than L2 ({a.n * 96 * 4 / 1e9:.1f} GB store, {a.n * R * 4 / 1e9:.1f} GB graph)",
                    "graph": f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins=64, T_ins=48)"},
         "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "L": v["L"], "T": v["T"], "iters": v["iters"]}
                   for k, v in best.items()},
