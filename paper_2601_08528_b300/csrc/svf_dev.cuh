@@ -646,6 +646,65 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
             }
             __syncwarp();
         }
+        // FP32 / BF16 compile-time layouts with <= 3 chunks per lane (FP8 keeps
+        // the half-batch split, which measured better): each lane takes two
+        // rows at once (rows r and r + nteam), so every query chunk loaded
+        // from shared memory serves both and the two dependency chains
+        // interleave.  The pair's second row may need the second barrier.
+        constexpr bool PAIR = CT && (DT == SVF_F32 || DT == SVF_BF16) && (NCH + team_for(NCH) - 1) / team_for(NCH) <= 3;
+        if constexpr (PAIR) {
+            constexpr int TS = team_for(NCH), CPL = (NCH + TS - 1) / TS, NT = 32 / TS;
+            bool second = cnt <= h;
+            for (int r0 = 0; r0 < cnt; r0 += 2 * NT) {
+                if (!second && r0 + NT >= h) {
+                    uint32_t it = 0;
+                    while (!mbar_try_wait(S.mbar + 1, S.phase[1]))
+                        if (++it > kWaitLimit) return false;
+                    S.phase[1] ^= 1u;
+                    second = true;
+                }
+                const int ra = r0 + team, rb = r0 + NT + team;
+                const bool va = ra < cnt, vb = rb < cnt;
+                const uint8_t *rowa = S.buf + (size_t)(va ? ra : 0) * cb;
+                const uint8_t *rowb = S.buf + (size_t)(vb ? rb : 0) * cb;
+                float fa = 0.f, fb = 0.f, sa = 1.f, sb = 1.f;
+                uint32_t ia = 0, ib = 0;
+                uint64_t pa[2] = {0, 0}, pb[2] = {0, 0};
+                if (DT == SVF_FP8) {
+                    sa = *reinterpret_cast<const float *>(rowa + R.d);
+                    sb = *reinterpret_cast<const float *>(rowb + R.d);
+                }
+                uint4 xa[CPL], xb[CPL];
+#pragma unroll
+                for (int u = 0; u < CPL; u++) {
+                    const int c = sub + u * TS;
+                    if (c < NCH) {
+                        xa[u] = reinterpret_cast<const uint4 *>(rowa)[c];
+                        xb[u] = reinterpret_cast<const uint4 *>(rowb)[c];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < CPL; u++) {
+                    const int c = sub + u * TS;
+                    if (c < NCH) {
+                        chunk_acc<DT>(R.metric, xa[u], c, qf, qb, sa, fa, ia, pa);
+                        chunk_acc<DT>(R.metric, xb[u], c, qf, qb, sb, fb, ib, pb);
+                    }
+                }
+                fold_pacc<DT>(fa, pa);
+                fold_pacc<DT>(fb, pb);
+#pragma unroll
+                for (int m = TS >> 1; m > 0; m >>= 1) {
+                    fa += __shfl_xor_sync(kFull, fa, m);
+                    fb += __shfl_xor_sync(kFull, fb, m);
+                }
+                if (sub == 0) {
+                    if (va) keys[i0 + ra] = make_key(finish_key<DT>(R.metric, fa, ia, sa), list[i0 + ra] | flags);
+                    if (vb) keys[i0 + rb] = make_key(finish_key<DT>(R.metric, fb, ib, sb), list[i0 + rb] | flags);
+                }
+            }
+            continue;
+        }
         for (int r0 = 0; r0 < cnt; r0 += nteam) {
             if (r0 == h) {  // the second half
                 uint32_t it = 0;
