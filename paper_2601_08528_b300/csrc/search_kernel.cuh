@@ -36,14 +36,20 @@ constexpr int kFastInsert = 8;
 __device__ __forceinline__ uint32_t hash_slot(uint32_t id, int bits) { return (id * 0x9E3779B1u) >> (32 - bits); }
 
 // Insert id; true if it was not present.  The table is kept at most half
-// full, so the probe always ends; the bound is only a guard.
+// full, so the probe always ends; the bound is only a guard.  A plain read
+// comes first: a slot that already holds a value needs no atomic (values are
+// only ever written into empty slots until the table is reset).
 __device__ __forceinline__ bool ht_insert(uint32_t *ht, int bits, uint32_t id) {
     const uint32_t mask = (1u << bits) - 1u;
     uint32_t h = hash_slot(id, bits);
     for (uint32_t p = 0; p <= mask; p++) {
-        uint32_t old = atomicCAS(ht + h, kEmpty, id);
-        if (old == kEmpty) return true;
-        if (old == id) return false;
+        const uint32_t cur = *reinterpret_cast<volatile uint32_t *>(ht + h);
+        if (cur == id) return false;
+        if (cur == kEmpty) {
+            const uint32_t old = atomicCAS(ht + h, kEmpty, id);
+            if (old == kEmpty) return true;
+            if (old == id) return false;
+        }
         h = (h + 1) & mask;
     }
     return false;
