@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-rates", default="25,50,100,200")
     ap.add_argument("--serve-form", default="fp32", choices=["fp32", "fp8"],
                     help="serving traversal: fp32 rows through the tier, or a resident fp8 copy + exact re-rank")
+    ap.add_argument("--serve-lins", type=int, default=128, help="insert search pool of the 50M build")
+    ap.add_argument("--serve-tins", type=int, default=96, help="insert search iterations of the 50M build")
     return ap.parse_args()
 
 
@@ -356,14 +358,14 @@ def serve_main(a, svf, torch, log_t):
     ix.build(torch.from_numpy(X[:N_BOOT]).cuda())
     while ix.n_used < n:
         b = min(ix.n_used, MAX_BATCH, n - ix.n_used)
-        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=64, T_ins=48)
+        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=a.serve_lins, T_ins=a.serve_tins)
     torch.cuda.synchronize()
     log_t("built")
     Qe = torch.from_numpy(synth.sample_chunked("serve128", 2000, 502)).cuda()
     gt = exact_knn(svf, ix.vectors()[:n], Qe, K, "l2")
     from paper_2601_08528_b300.learned import recall_at_k
     op = None
-    for L, T in [(64, 64), (64, 96), (128, 64), (128, 96), (256, 128), (256, 192)]:
+    for L, T in [(64, 64), (64, 96), (128, 64), (128, 96), (256, 128), (256, 192), (256, 256), (256, 384)]:
         cfg = svf.SearchConfig(k=K, L=L, T=T, precision=a.serve_form if lowp else None, rerank=bool(lowp))
         r = recall_at_k(ix.search(Qe, cfg)[0], gt)
         log_t(f"  L={L} T={T} recall={r:.4f}")
@@ -387,6 +389,7 @@ def serve_main(a, svf, torch, log_t):
     out = {"metric": "serving p99 search latency (ms) at offered load", "value": min(p99) if p99 else None,
            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
            "config": {"workload": "serve128-50M", "form": a.serve_form, "n": n, "d": 128, "R": R,
+                      "build": f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins={a.serve_lins}, T_ins={a.serve_tins})",
                       "cache_rows": slots, "L": cfg.L,
                       "T": cfg.T, "recall@10": rec, "mix": "90:9:1", "batch": "log-uniform 1..2048",
                       "queries": "Zipf(1.1) over components"},
