@@ -1,0 +1,151 @@
+"""The measured configurations at full size, checked on outputs the oracle can
+compute one at a time, and by properties that hold at any size.
+
+* unit96, 10M x 96 inner product, R = 32, built as the benchmark builds it
+  (exact build of 200,000 rows, then inserts of the rest); 10,000 queries
+  searched in the benchmark's launch configuration (L = 64, T = 96), plain
+  FP32 and FP8 traversal + exact FP32 re-rank; a sample of the queries is
+  searched by the FP64 oracle on the same graph.
+* u8, 1M x 128 uint8 squared L2, R = 64: the GPU's exact build checked row
+  by row on sampled vertices (exact 128-NN + prune by the oracle), sampled
+  searches bit-exact, and one insert batch of 10,000 vectors compared over the
+  whole graph with the oracle's insert of the same batch.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N96, NQ, SEED = 10_000_000, 10_000, 4
+
+
+@pytest.fixture(scope="module")
+def svf():
+    import paper_2601_08528_b300 as svf
+    svf.load()
+    return svf
+
+
+@pytest.fixture(scope="module")
+def unit96(svf):
+    X = synth.sample_chunked("unit96", N96, 300)
+    ix = svf.Index(96, N96, dtype="f32", metric="ip", R=32, lowp=("fp8",), max_batch=1_000_000)
+    ix.build(torch.from_numpy(X[:200_000]).cuda())
+    while ix.n_used < N96:
+        b = min(ix.n_used, 1_000_000, N96 - ix.n_used)
+        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=64, T_ins=48)
+    torch.cuda.synchronize()
+    g = P.as_u32(ix.graph[:N96].cpu().numpy())
+    Q = synth.sample_chunked("unit96", NQ, 302)
+    return X, ix, g, Q
+
+
+def graph_invariants(g, n):
+    """Fixed degree: every entry is a live id < n or EMPTY; no self loops; no
+    id twice in a row."""
+    empty = np.uint32(0xFFFFFFFF)
+    assert ((g < n) | (g == empty)).all()
+    rows = np.arange(len(g), dtype=np.uint32)[:, None]
+    assert not (g == rows).any(), "self loop"
+    s = np.sort(g, axis=1)
+    dup = (s[:, 1:] == s[:, :-1]) & (s[:, 1:] != empty)
+    assert not dup.any(), f"{dup.any(1).sum()} rows repeat an id"
+
+
+def test_unit96_10M_graph_invariants(unit96):
+    X, ix, g, Q = unit96
+    graph_invariants(g, N96)
+    # the insert path fills every row of a connected build
+    assert (g != 0xFFFFFFFF).sum(1).min() > 0
+
+
+def sample(nq, m, seed):
+    return np.sort(np.random.default_rng(seed).choice(nq, m, replace=False))
+
+
+def test_unit96_10M_fp32_search_sampled(svf, orc, unit96):
+    X, ix, g, Q = unit96
+    ids, dist = ix.search(torch.from_numpy(Q).cuda(), svf.SearchConfig(k=10, L=64, T=96, seed=SEED))
+    qs = sample(NQ, 48, 11)
+    st = orc.Store.from_vectors(X, "ip")
+    o = orc.search(st, N96, g, None, Q[qs], 10, 64, 96, SEED)
+    P.check_fp32(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], o, X, Q[qs], "ip")
+
+
+def test_unit96_10M_fp8_rerank_search_sampled(svf, orc, unit96):
+    X, ix, g, Q = unit96
+    L = 64
+    ids, dist = ix.search(torch.from_numpy(Q).cuda(),
+                          svf.SearchConfig(k=10, L=L, T=96, precision="fp8", rerank=True, seed=SEED))
+    qs = sample(NQ, 48, 12)
+    lst = orc.Store.from_vectors(X, "ip", dtype="fp8")
+    o = orc.search(lst, N96, g, None, Q[qs], 10, L, 96, SEED, want_pool=True)
+    # oracle: exact FP64 distances of the final fp8-traversal pool, re-sorted by (dist, id)
+    st = orc.Store.from_vectors(X, "ip")
+    pd = orc.dist_ids(st, Q[qs], o["pool_ids"])
+    want_i = np.empty((len(qs), 10), np.int64)
+    want_d = np.empty((len(qs), 10))
+    gaps = np.empty(len(qs))
+    for q in range(len(qs)):
+        order = np.lexsort((o["pool_ids"][q], pd[q]))
+        want_i[q] = o["pool_ids"][q][order[:10]]
+        want_d[q] = pd[q][order[:10]]
+        s = pd[q][order[:11]]
+        gaps[q] = np.min(np.abs(np.diff(s))) if len(s) > 1 else np.inf
+    ref = {"ids": want_i, "dist": want_d, "gap": np.minimum(gaps, o["gap"])}
+    P.check_fp32(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], ref, X, Q[qs], "ip")
+
+
+# ---------------------------------------------------------------- uint8, 1M x 128, R = 64
+N8, R8, B8 = 1_000_000, 64, 10_000
+
+
+@pytest.fixture(scope="module")
+def u8(svf):
+    X = synth.sample_chunked("u8", N8 + B8, 201)
+    ix = svf.Index(128, N8 + B8, dtype="u8", metric="l2", R=R8, max_batch=N8)
+    ix.build(torch.from_numpy(X[:N8]).cuda())
+    torch.cuda.synchronize()
+    g = P.as_u32(ix.graph[:N8].cpu().numpy())
+    return X, ix, g
+
+
+def test_u8_1M_build_rows_sampled(orc, u8):
+    X, ix, g = u8
+    graph_invariants(g, N8)
+    vs = sample(N8, 24, 21)
+    st = orc.Store.from_vectors(X[:N8], "l2")
+    ids, d, _ = orc.knn(st, X[vs], 2 * R8, self_ids=vs.astype(np.int64))
+    for i, v in enumerate(vs):
+        row, _ = orc.prune(st, ids[i], d[i], R8)
+        np.testing.assert_array_equal(g[v], row, err_msg=f"row {v}")
+
+
+def test_u8_1M_search_sampled_bit_exact(svf, orc, u8):
+    X, ix, g = u8
+    Q = synth.sample_chunked("u8", NQ, 202)
+    for L in (64, 128):
+        ids, dist = ix.search(torch.from_numpy(Q).cuda(), svf.SearchConfig(k=10, L=L, T=L // 2, seed=SEED))
+        qs = sample(NQ, 48, 30 + L)
+        st = orc.Store.from_vectors(X[:N8], "l2")
+        o = orc.search(st, N8, g, None, Q[qs], 10, L, L // 2, SEED)
+        P.check_exact(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], o)
+
+
+def test_u8_1M_insert_batch_whole_graph(svf, orc, u8):
+    X, ix, g = u8
+    st = orc.Store.from_vectors(X, "l2")
+    want = np.zeros((N8 + B8, R8), dtype=np.uint32)
+    want[:N8] = g
+    new = ix.insert(torch.from_numpy(X[N8:N8 + B8]).cuda(), L_ins=128, T_ins=64)
+    assert new.cpu().numpy().tolist() == list(range(N8, N8 + B8))
+    orc.insert(st, N8, B8, want, None, 128, 64, ix.params.seed)
+    got = P.as_u32(ix.graph[:N8 + B8].cpu().numpy())
+    bad = np.where((got != want).any(1))[0]
+    assert len(bad) == 0, f"{len(bad)} rows differ, e.g. {bad[:5]}"
+    graph_invariants(got, N8 + B8)
