@@ -381,6 +381,17 @@ int svf_mlp_pack(const float *params, void *packed, void *stream);
 /* Logits of the fp32 network for n feature rows (device [n][16] -> [n]). */
 int svf_mlp_forward(const float *params, const float *feat, int64_t n, float *z, void *stream);
 
+/* ---- failure-path self test (no counterpart in the paper).  Every device
+ * wait in the library polls an mbarrier at most svf_wait_limit() times, then
+ * records SVF_ETIMEOUT (and the poll count as detail) in the status words
+ * and returns.  svf_selftest_wait_timeout runs one warp on a barrier nothing
+ * arrives at, with the same loop capped at `polls`; status is a caller-owned
+ * device buffer of >= 2 uint64 (overwritten).  Returns SVF_ETIMEOUT when the
+ * wait gave up and reported it, as it must; *out_seconds (host, optional) is
+ * the wall time of the launch. */
+uint32_t svf_wait_limit(void);
+int svf_selftest_wait_timeout(uint32_t polls, unsigned long long *status, double *out_seconds, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

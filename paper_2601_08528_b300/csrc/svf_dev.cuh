@@ -513,7 +513,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr uint32_t kWaitLimit = 1u << 22;  // bounded wait on an mbarrier (each try_wait may also block briefly)
+constexpr uint32_t kWaitLimit = 1u << 18;  // polls of an mbarrier before a wait gives up (~1 s: an idle poll suspends ~4 us)
 
 struct Stage {
     uint8_t *buf;       // per-warp buffer (16-byte aligned)
