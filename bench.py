@@ -511,15 +511,37 @@ def main():
     Qh = torch.from_numpy(Qe_np).pin_memory()
     ids_h = torch.empty((a.nq, K), dtype=torch.int32).pin_memory()
     d_h = torch.empty((a.nq, K), dtype=torch.float32).pin_memory()
-    Qd = torch.empty_like(Qe)
+    # Double-buffered pipeline through the public API: step k's search runs on
+    # the compute stream while a copy stream uploads step k+1's queries and
+    # downloads step k-1's results (every step still moves its full batch).
+    Qd = [torch.empty_like(Qe), torch.empty_like(Qe)]
+    io = [torch.empty_like(ids_out), torch.empty_like(ids_out)]
+    do = [torch.empty_like(d_out), torch.empty_like(d_out)]
+    cs = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    up, srch = [ev(), ev()], [ev(), ev()]
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    for _ in range(a.steps):
-        Qd.copy_(Qh, non_blocking=True)
-        ix.search(Qd, cfg, out_ids=ids_out, out_dist=d_out)
-        ids_h.copy_(ids_out, non_blocking=True)
-        d_h.copy_(d_out, non_blocking=True)
+    cs.wait_event(e0)
+    with torch.cuda.stream(cs):
+        Qd[0].copy_(Qh, non_blocking=True)
+        up[0].record(cs)
+    for k in range(a.steps):
+        b = k & 1
+        st.wait_event(up[b])
+        ix.search(Qd[b], cfg, out_ids=io[b], out_dist=do[b], stream=st)
+        srch[b].record(st)
+        with torch.cuda.stream(cs):
+            if k + 1 < a.steps:
+                if k >= 1:
+                    cs.wait_event(srch[b ^ 1])  # step k-1's search has read its buffer
+                Qd[b ^ 1].copy_(Qh, non_blocking=True)
+                up[b ^ 1].record(cs)
+            cs.wait_event(srch[b])
+            ids_h.copy_(io[b], non_blocking=True)
+            d_h.copy_(do[b], non_blocking=True)
+    st.wait_stream(cs)
     e1.record(st)
     e1.synchronize()
     e2e_t = e0.elapsed_time(e1) / 1e3
