@@ -140,6 +140,9 @@ STOP_POINTS = [(64, 96), (64, 128), (128, 64), (128, 72), (128, 80), (128, 96)]
 STOP_EVERY = 4
 
 
+METRIC = "search QPS at recall@10>=0.95 (plain FP32 vs BF16/FP8 + learned stop)"
+
+
 def unit96_name(n):
     return f"unit96-{n // 1_000_000}M" if n % 1_000_000 == 0 else f"unit96-{n}"
 
@@ -447,7 +450,7 @@ def main():
                 steps.append(q)
         v = statistics.median(steps)
         sample = f"{m_used} of {a.nq} queries per step, fixed-T FP64 search at L={op['L']} T={op['T']} on the GPU-built graph"
-        out = {"impl": "reference", "metric": "search QPS at recall@10>=0.95", "value": v, "unit": "queries/s",
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
                "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": unit96_name(a.n), "n": a.n, "d": 96, "R": R, "nq": a.nq, "k": K, "L": op["L"],
@@ -559,7 +562,7 @@ def main():
     peaks, src = measured_peaks()
     achieved = alg / mean_launch / 1e9
     out = {
-        "metric": "search QPS at recall@10>=0.95 (plain FP32 vs BF16/FP8 + learned stop)",
+        "metric": METRIC,
         "value": world * nq * a.steps / total,
         "unit": "queries/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
