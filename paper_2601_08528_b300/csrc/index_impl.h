@@ -24,10 +24,11 @@ inline int esize_of(int dtype) { return dtype == SVF_U8 ? 1 : 4; }
 inline int64_t fp8_pitch(int d) { return ((int64_t)d + 4 + 31) / 32 * 32; }
 
 // Lanes per row when distances are computed from staged rows: the smallest
-// power of two that leaves at most 4 chunks of 16 bytes per lane.
+// power of two that leaves at most max_chunks_per_lane(dtype) chunks of 16
+// bytes per lane (8 for FP8 rows, 4 otherwise).
 inline void set_team(RowDesc &r) {
     int ts = 1;
-    while (ts < 32 && (r.nchunk + ts - 1) / ts > 4) ts <<= 1;
+    while (ts < 32 && (r.nchunk + ts - 1) / ts > max_chunks_per_lane(r.dtype)) ts <<= 1;
     r.ts = ts;
     r.cpl = (r.nchunk + ts - 1) / ts;
 }

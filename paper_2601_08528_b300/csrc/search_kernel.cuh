@@ -485,8 +485,8 @@ constexpr int nch_for_dim(int d) {
 }
 template <int DT, int NCH>
 bool layout_is(const RowDesc &r) {
-    return r.nchunk == NCH && r.copy_bytes == staged_row_bytes<DT, NCH>() && r.ts == team_for(NCH) &&
-           r.cpl == (NCH + team_for(NCH) - 1) / team_for(NCH);
+    return r.nchunk == NCH && r.copy_bytes == staged_row_bytes<DT, NCH>() && r.ts == team_for(NCH, DT) &&
+           r.cpl == (NCH + team_for(NCH, DT) - 1) / team_for(NCH, DT);
 }
 
 // Dispatch on R, learned features and the row layout (specialised for the

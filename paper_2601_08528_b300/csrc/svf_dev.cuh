@@ -553,9 +553,12 @@ __device__ __forceinline__ void tier_miss(const TierCtx &T, uint32_t id) {
 // Staged-row layout known at compile time (NCH 16-byte value chunks per
 // row): the team size and chunks per lane of set_team, and the staged row
 // bytes (values, plus the scale slot for FP8).
-__host__ __device__ constexpr int team_for(int nch) {
+// Chunks per lane at most: 8 for FP8 rows (one lane per d = 96 or 128 row,
+// no team reduction), 4 otherwise.
+__host__ __device__ constexpr int max_chunks_per_lane(int dtype) { return dtype == SVF_FP8 ? 8 : 4; }
+__host__ __device__ constexpr int team_for(int nch, int dtype) {
     int ts = 1;
-    while (ts < 32 && (nch + ts - 1) / ts > 4) ts <<= 1;
+    while (ts < 32 && (nch + ts - 1) / ts > max_chunks_per_lane(dtype)) ts <<= 1;
     return ts;
 }
 template <int DT, int NCH>
@@ -576,9 +579,9 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
     constexpr bool CT = NCH > 0;
     const int cb = CT ? staged_row_bytes<DT, NCH>() : R.copy_bytes;
     const int nch = CT ? NCH : R.nchunk;
-    const int cpl = CT ? (NCH + team_for(NCH) - 1) / team_for(NCH) : R.cpl;
+    const int cpl = CT ? (NCH + team_for(NCH, DT) - 1) / team_for(NCH, DT) : R.cpl;
     const int per = (int)(S.cap / (uint32_t)cb);
-    const int ts = CT ? team_for(NCH) : R.ts, team = lane / ts, sub = lane % ts, nteam = 32 / ts;
+    const int ts = CT ? team_for(NCH, DT) : R.ts, team = lane / ts, sub = lane % ts, nteam = 32 / ts;
     for (int i0 = 0; i0 < n; i0 += per) {
         const int cnt = min(per, n - i0);
         __syncwarp();
@@ -651,9 +654,9 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
         // rows at once (rows r and r + nteam), so every query chunk loaded
         // from shared memory serves both and the two dependency chains
         // interleave.  The pair's second row may need the second barrier.
-        constexpr bool PAIR = CT && (DT == SVF_F32 || DT == SVF_BF16) && (NCH + team_for(NCH) - 1) / team_for(NCH) <= 3;
+        constexpr bool PAIR = CT && (DT == SVF_F32 || DT == SVF_BF16) && (NCH + team_for(NCH, DT) - 1) / team_for(NCH, DT) <= 3;
         if constexpr (PAIR) {
-            constexpr int TS = team_for(NCH), CPL = (NCH + TS - 1) / TS, NT = 32 / TS;
+            constexpr int TS = team_for(NCH, DT), CPL = (NCH + TS - 1) / TS, NT = 32 / TS;
             bool second = cnt <= h;
             for (int r0 = 0; r0 < cnt; r0 += 2 * NT) {
                 if (!second && r0 + NT >= h) {
@@ -719,19 +722,20 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
             uint32_t iacc = 0;
             uint64_t pacc[2] = {0, 0};
             if (DT == SVF_FP8) scale = *reinterpret_cast<const float *>(row + R.d);
-            uint4 v[4];
+            constexpr int MC = max_chunks_per_lane(DT);
+            uint4 v[MC];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
+            for (int u = 0; u < MC; u++) {
                 const int c = sub + u * ts;
                 if (valid && u < cpl && c < nch) v[u] = reinterpret_cast<const uint4 *>(row)[c];
             }
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
+            for (int u = 0; u < MC; u++) {
                 const int c = sub + u * ts;
                 if (valid && u < cpl && c < nch)
                     chunk_acc<DT>(R.metric, v[u], c, qf, qb, scale, facc, iacc, pacc);
             }
-            for (int c0 = sub + 4 * ts; c0 < nch; c0 += ts)  // rows longer than 4 chunks per lane
+            for (int c0 = sub + MC * ts; c0 < nch; c0 += ts)  // rows longer than MC chunks per lane
                 if (valid)
                     chunk_acc<DT>(R.metric, reinterpret_cast<const uint4 *>(row)[c0], c0, qf, qb, scale, facc, iacc,
                                   pacc);
