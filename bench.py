@@ -64,16 +64,20 @@ def parse():
     ap.add_argument("--serve-rates", default="25,50,100,200")
     ap.add_argument("--serve-form", default="fp32", choices=["fp32", "fp8"],
                     help="serving traversal: fp32 rows through the tier, or a resident fp8 copy + exact re-rank")
+    ap.add_argument("--serve-policies", default="",
+                    help="comma list of extra cache placement policies (clock,lfu,static) run on the same serving "
+                         "stream after WAVP, for the ablation")
     ap.add_argument("--serve-lins", type=int, default=128, help="insert search pool of the 50M build")
     ap.add_argument("--serve-tins", type=int, default=96, help="insert search iterations of the 50M build")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- setup
-def build_index(svf, torch, X, log_t):
+def build_index(svf, torch, X, log_t, streams=1):
     n = X.shape[0]
-    # headroom for the serving stream's inserts
-    ix = svf.Index(96, n + 300_000, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"), max_batch=MAX_BATCH)
+    # headroom for the serving streams' inserts
+    ix = svf.Index(96, n + 300_000 * streams, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"),
+                   max_batch=MAX_BATCH)
     n0 = min(N_BOOT, n)
     t = time.time()
     ix.build(torch.from_numpy(X[:n0]).cuda())
@@ -427,7 +431,8 @@ def main():
     X = synth.sample_chunked("unit96", a.n, 300)
     Qe_np = synth.sample_chunked("unit96", a.nq, 302 + rank)
     log_t("data", X.shape)
-    ix = build_index(svf, torch, X, log_t)
+    policies = [p for p in a.serve_policies.split(",") if p]
+    ix = build_index(svf, torch, X, log_t, streams=1 + len(policies))
     Xd = ix.vectors()[:a.n]
     Qe = torch.from_numpy(Qe_np).cuda()
     gt = exact_knn(svf, Xd, Qe, K, "ip")
@@ -589,13 +594,25 @@ def main():
     # fp8 traversal resident, exact re-rank through the tier; an open-loop
     # Poisson stream of uneven batches with inserts and deletes
     if a.serve_rate > 0:
-        ix.enable_tier(M=int(a.n * 0.3125), theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
+        tier = dict(M=int(a.n * 0.3125), theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
+        ix.enable_tier(**tier)
         X_ins = synth.sample_chunked("unit96", 200_000, 305)
         out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg)
         out["serving"]["workload"] = ("unit96-10M tiered: fp32 rows in pinned host memory behind a 3.1M-row device "
                                       "cache, fp8 traversal + exact re-rank, Zipf(1.1) queries, 90:9:1 mix, "
                                       "batches log-uniform 1..2048")
+        out["serving"]["policy"] = "wavp"
         log_t("serving", json.dumps(out["serving"]))
+        # placement ablation: the same stream (same seed) after re-tiering the
+        # same index under each other policy
+        if policies:
+            out["serving_policies"] = {"wavp": out["serving"]}
+            for p in policies:
+                ix.reset_tier(policy=p, **tier)
+                r = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg)
+                r["policy"] = p
+                out["serving_policies"][p] = r
+                log_t("serving", p, json.dumps(r))
     # deletes (1% of the index, uniformly drawn live ids) with localized repair
     dels = torch.from_numpy(synth.pick_live_ids(a.n, None, a.n // 100, 304).view(np.int32)).cuda()
     torch.cuda.synchronize()

@@ -243,6 +243,14 @@ int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, 
  * copies (lowp) stay whole in device memory and are encoded from the
  * inserted rows, so BF16/FP8 traversal reads no host memory and only the
  * exact re-rank goes through the tier. */
+/* Placement policies (svf_tier_params.policy).  WAVP is the paper's
+ * (Alg. 2, Eq. 2); the others are ablations of it on the same machinery:
+ * CLOCK admits every missed row in miss order and evicts the first
+ * unreferenced slots the clock meets (second chance: recency only); LFU
+ * admits and evicts by F_recent alone (beta ignored, theta fixed at theta0);
+ * STATIC keeps the cold-start cache of the highest in-degree rows. */
+enum svf_tier_policy { SVF_TIER_WAVP = 0, SVF_TIER_CLOCK = 1, SVF_TIER_LFU = 2, SVF_TIER_STATIC = 3 };
+
 typedef struct {
     int64_t M;              /* cache slots */
     uint32_t qcap;          /* promotion queue capacity (<= 16384) */
@@ -251,6 +259,8 @@ typedef struct {
     float alpha, beta;      /* Eq. 2 weights (paper: alpha/(alpha+beta) ~ 0.6) */
     float theta0;           /* initial promotion threshold */
     uint64_t decay_every;   /* halve F_recent after this many misses */
+    int32_t policy;         /* svf_tier_policy */
+    int32_t reserved0;
 } svf_tier_params;
 
 typedef struct {
@@ -271,6 +281,12 @@ int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buff
 int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream);
 /* Current promotion threshold. */
 float svf_tier_theta(svf_index *h);
+/* Re-initialise a tiered store with new parameters (policy, weights,
+ * threshold; M and the buffers stay): miss counts, queue and reference bits
+ * are cleared, E_in is recomputed from the current graph and the cache is
+ * warmed again with the highest in-degree rows, read from the host store.
+ * Must not run while a search or update on the index is in flight. */
+int svf_tier_reset(svf_index *h, const svf_tier_params *tp, void *stream);
 
 /* ---- continuous-batching request loop (Sec. 4.4 real-time coordination,
  * Sec. 5.3 consistency).  A worker thread admits requests in submission

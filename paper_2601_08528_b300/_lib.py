@@ -23,7 +23,7 @@ MLP_PARAMS, MLP_PACKED = 1153, 1160
 SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "svf_attach", "svf_build", "svf_search",
            "svf_insert", "svf_delete", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
            "svf_encode_fp8", "svf_knn", "svf_mlp_grad", "svf_mlp_partial_floats", "svf_mlp_adam", "svf_mlp_pack",
-           "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta",
+           "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta", "svf_tier_reset",
            "svf_serve_now", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
            "svf_serve_stop", "svf_knn_tc_scratch_bytes", "svf_knn_tc", "svf_wait_limit", "svf_selftest_wait_timeout"]
 
@@ -62,7 +62,11 @@ class Counters(C.Structure):
 
 class TierParams(C.Structure):
     _fields_ = [("M", C.c_int64), ("qcap", C.c_uint32), ("promote_batch", C.c_int32), ("sweep", C.c_int32),
-                ("alpha", C.c_float), ("beta", C.c_float), ("theta0", C.c_float), ("decay_every", C.c_uint64)]
+                ("alpha", C.c_float), ("beta", C.c_float), ("theta0", C.c_float), ("decay_every", C.c_uint64),
+                ("policy", C.c_int32), ("reserved0", C.c_int32)]
+
+
+TIER_POLICIES = {"wavp": 0, "clock": 1, "lfu": 2, "static": 3}
 
 
 class TierSizes(C.Structure):
@@ -135,6 +139,7 @@ def load() -> C.CDLL:
         "svf_tier_enable": (I32, [P, C.POINTER(TierParams), C.POINTER(TierBuffers), P]),
         "svf_tier_maintain": (I32, [P, C.POINTER(C.c_int64), P]),
         "svf_tier_theta": (C.c_float, [P]),
+        "svf_tier_reset": (I32, [P, C.POINTER(TierParams), P]),
         "svf_serve_now": (C.c_double, []),
         "svf_serve_start": (I32, [P, C.POINTER(ServeCfg), C.POINTER(C.c_void_p)]),
         "svf_serve_submit": (I32, [P, C.POINTER(Request)]),

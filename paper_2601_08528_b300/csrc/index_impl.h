@@ -2,6 +2,7 @@
 // api.cu and tier.cu): parameters, borrowed buffers, workspace layout, and
 // the row descriptors of the stores.
 #pragma once
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -62,6 +63,7 @@ struct Tier {
     uint64_t *scratch = nullptr;  // maintenance keys
     float alpha = 0.6f, beta = 0.4f, theta = 2.0f, theta0 = 2.0f;
     int promote_batch = 2048, sweep = 4;
+    int policy = SVF_TIER_WAVP;
     uint64_t decay_every = 1 << 16;
     int64_t clock = 0;
     uint64_t last_hits = 0, last_misses = 0, misses_at_decay = 0, rounds = 0;
@@ -123,9 +125,13 @@ struct svf_index {
         t.queue = tier.queue;
         t.qcount = status() + svf::kStQCount;
         t.qcap = tier.qcap;
-        t.alpha = tier.alpha;
-        t.beta = tier.beta;
-        t.theta = tier.theta;
+        // what a miss queues: Eq. 2 over theta (WAVP), every miss (CLOCK),
+        // F_recent over the fixed theta (LFU), nothing (STATIC)
+        t.alpha = tier.policy == SVF_TIER_WAVP ? tier.alpha : 1.f;
+        t.beta = tier.policy == SVF_TIER_WAVP ? tier.beta : 0.f;
+        t.theta = tier.policy == SVF_TIER_CLOCK    ? -1.f
+                  : tier.policy == SVF_TIER_STATIC ? INFINITY
+                                                   : tier.theta;
         return t;
     }
 };

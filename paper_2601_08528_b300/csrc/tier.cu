@@ -70,8 +70,10 @@ __global__ void fill_slots_kernel(const uint8_t *src, int64_t pitch, const int32
 }
 
 // Promotion candidates ordered by descending F_lambda (ties by id).
+// by_order (CLOCK): in queue (miss) order instead.
 __global__ void score_queue_kernel(const uint32_t *queue, int64_t c, int64_t npow, const uint32_t *freq,
-                                   const uint32_t *ein, float alpha, float beta, uint64_t *keys, float *fsum) {
+                                   const uint32_t *ein, float alpha, float beta, int by_order, uint64_t *keys,
+                                   float *fsum) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npow) return;
     if (i >= c) {
@@ -80,16 +82,17 @@ __global__ void score_queue_kernel(const uint32_t *queue, int64_t c, int64_t npo
     }
     const uint32_t x = queue[i];
     const float f = flambda(alpha, beta, freq[x], ein[x]);
-    keys[i] = make_key(~fkey(f), x);
+    keys[i] = by_order ? make_key((uint32_t)i, x) : make_key(~fkey(f), x);
     atomicAdd(fsum, f);
 }
 
 // Clock sweep over W slots from the hand: referenced slots lose their bit;
 // unreferenced ones become victims ordered by ascending F_lambda of their
-// owner (empty slots first).
+// owner (empty slots first), or (by_order: CLOCK) in the order the clock
+// meets them.
 __global__ void victim_kernel(const int32_t *owner, uint8_t *ref, const uint32_t *freq, const uint32_t *ein,
                               int64_t M, int64_t hand, int64_t W, int64_t npow, float alpha, float beta,
-                              uint64_t *keys, unsigned long long *nvalid) {
+                              int by_order, uint64_t *keys, unsigned long long *nvalid) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npow) return;
     if (i >= W) {
@@ -103,8 +106,12 @@ __global__ void victim_kernel(const int32_t *owner, uint8_t *ref, const uint32_t
         return;
     }
     const int32_t o = owner[s];
-    const float f = o < 0 ? -INFINITY : flambda(alpha, beta, freq[o], ein[o]);
-    keys[i] = make_key(fkey(f), (uint32_t)s);
+    if (by_order) {
+        keys[i] = make_key(o < 0 ? 0u : (uint32_t)i + 1u, (uint32_t)s);
+    } else {
+        const float f = o < 0 ? -INFINITY : flambda(alpha, beta, freq[o], ein[o]);
+        keys[i] = make_key(fkey(f), (uint32_t)s);
+    }
     atomicAdd(nvalid, 1ull);
 }
 
@@ -178,6 +185,60 @@ int64_t pow2_at_least(int64_t x) {
 
 unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Parameters, cleared tables, E_in from the graph, and the cold-start cache
+// of the highest in-degree rows (rows read from `src`: the device store at
+// enable, the host store at reset).  Synchronises the stream.
+int tier_init(svf_index *h, const svf_tier_params *tp, const uint8_t *src, cudaStream_t st) {
+    Tier &T = h->tier;
+    const int64_t n = h->n_used, R = h->p.R;
+    const int64_t pitch = (int64_t)h->p.d * esize_of(h->p.dtype);
+    T.qcap = tp->qcap;
+    T.alpha = tp->alpha;
+    T.beta = tp->beta;
+    T.theta = T.theta0 = tp->theta0;
+    T.promote_batch = tp->promote_batch;
+    T.sweep = tp->sweep;
+    T.decay_every = tp->decay_every ? tp->decay_every : (1ull << 16);
+    T.policy = tp->policy;
+    T.clock = 0;
+    T.rounds = 0;
+    T.last_rate = T.last_meanf = 0.0;
+    CUDA_TRY(cudaMemsetAsync(T.map, 0xFF, (size_t)h->p.n_cap * 4, st));
+    CUDA_TRY(cudaMemsetAsync(T.owner, 0xFF, (size_t)T.M * 4, st));
+    CUDA_TRY(cudaMemsetAsync(T.ref, 0, (size_t)T.M, st));
+    CUDA_TRY(cudaMemsetAsync(T.freq, 0, (size_t)h->p.n_cap * 4, st));
+    CUDA_TRY(cudaMemsetAsync(T.ein, 0, (size_t)h->p.n_cap * 4, st));
+    CUDA_TRY(cudaMemsetAsync(h->status() + kStQCount, 0, 8, st));
+    if (n) {
+        ein_kernel<<<grid_for(n * R, 256), 256, 0, st>>>(h->b.graph, n, (int)R, h->b.del_bits, T.ein);
+        unsigned long long *hist = reinterpret_cast<unsigned long long *>(T.scratch + kMaxQueue + kMaxSweep);
+        CUDA_TRY(cudaMemsetAsync(hist, 0, kHistBins * 8 + 16, st));
+        hist_kernel<<<296, 256, 0, st>>>(T.ein, n, hist);
+        std::vector<unsigned long long> hh(kHistBins);
+        CUDA_TRY(cudaMemcpyAsync(hh.data(), hist, kHistBins * 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        unsigned long long above = 0;
+        int thr = kHistBins - 1;
+        const unsigned long long M = (unsigned long long)std::min<int64_t>(T.M, n);
+        for (; thr >= 0; thr--) {
+            if (above + hh[thr] >= M) break;
+            above += hh[thr];
+        }
+        if (thr < 0) thr = 0;
+        const unsigned long long quota = M - std::min(M, above);
+        unsigned long long *cnt = hist + kHistBins;
+        warm_assign_kernel<<<grid_for(n, 256), 256, 0, st>>>(T.ein, n, (uint32_t)thr, quota, T.map, T.owner, cnt);
+        fill_slots_kernel<<<grid_for(T.M * 32, 256), 256, 0, st>>>(src, pitch, T.owner, T.M, T.cache);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(st));
+    unsigned long long s[kStWords];
+    CUDA_TRY(cudaMemcpy(s, h->status(), sizeof s, cudaMemcpyDeviceToHost));
+    T.last_hits = s[kStHits];
+    T.last_misses = T.misses_at_decay = s[kStMisses];
+    return SVF_OK;
+}
+
 }  // namespace
 }  // namespace svf
 
@@ -192,6 +253,7 @@ int svf_tier_buffer_sizes(const svf_params *p, const svf_tier_params *tp, svf_ti
     if (tp->promote_batch < 1 || tp->promote_batch > 2048) return fail(SVF_EINVAL, "promote_batch in [1, 2048]");
     if (tp->sweep < 1 || (int64_t)tp->sweep * tp->promote_batch > kMaxSweep)
         return fail(SVF_EINVAL, "sweep * promote_batch must be <= 8192");
+    if (tp->policy < SVF_TIER_WAVP || tp->policy > SVF_TIER_STATIC) return fail(SVF_EINVAL, "unknown tier policy");
     const int64_t pitch = (int64_t)p->d * esize_of(p->dtype);
     out->cache = align256((size_t)tp->M * pitch);
     out->map = align256((size_t)p->n_cap * 4);
@@ -217,7 +279,7 @@ int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buff
     cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
     Tier &T = h->tier;
-    const int64_t n = h->n_used, R = h->p.R;
+    const int64_t n = h->n_used;
     const int64_t pitch = (int64_t)h->p.d * esize_of(h->p.dtype);
     T.host = reinterpret_cast<uint8_t *>(tb->host);
     T.cache = reinterpret_cast<uint8_t *>(tb->cache);
@@ -228,54 +290,25 @@ int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buff
     T.freq = tb->freq;
     T.ein = tb->ein;
     T.queue = tb->queue;
-    T.qcap = tp->qcap;
     T.scratch = reinterpret_cast<uint64_t *>(tb->scratch);
-    T.alpha = tp->alpha;
-    T.beta = tp->beta;
-    T.theta = T.theta0 = tp->theta0;
-    T.promote_batch = tp->promote_batch;
-    T.sweep = tp->sweep;
-    T.decay_every = tp->decay_every ? tp->decay_every : (1ull << 16);
-    T.clock = 0;
-    // host copy of the rows, tables reset
+    // host copy of the rows, then the tables and the warm cache
     if (n) CUDA_TRY(cudaMemcpyAsync(T.host, h->b.vecs, (size_t)n * pitch, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemsetAsync(T.map, 0xFF, (size_t)h->p.n_cap * 4, st));
-    CUDA_TRY(cudaMemsetAsync(T.owner, 0xFF, (size_t)T.M * 4, st));
-    CUDA_TRY(cudaMemsetAsync(T.ref, 0, (size_t)T.M, st));
-    CUDA_TRY(cudaMemsetAsync(T.freq, 0, (size_t)h->p.n_cap * 4, st));
-    CUDA_TRY(cudaMemsetAsync(T.ein, 0, (size_t)h->p.n_cap * 4, st));
-    CUDA_TRY(cudaMemsetAsync(h->status() + kStQCount, 0, 8, st));
-    // E_in and the cold-start selection of the highest in-degree rows
-    if (n) {
-        ein_kernel<<<grid_for(n * R, 256), 256, 0, st>>>(h->b.graph, n, (int)R, h->b.del_bits, T.ein);
-        unsigned long long *hist = reinterpret_cast<unsigned long long *>(T.scratch + kMaxQueue + kMaxSweep);
-        CUDA_TRY(cudaMemsetAsync(hist, 0, kHistBins * 8 + 16, st));
-        hist_kernel<<<296, 256, 0, st>>>(T.ein, n, hist);
-        std::vector<unsigned long long> hh(kHistBins);
-        CUDA_TRY(cudaMemcpyAsync(hh.data(), hist, kHistBins * 8, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-        unsigned long long above = 0;
-        int thr = kHistBins - 1;
-        const unsigned long long M = (unsigned long long)std::min<int64_t>(T.M, n);
-        for (; thr >= 0; thr--) {
-            if (above + hh[thr] >= M) break;
-            above += hh[thr];
-        }
-        if (thr < 0) thr = 0;
-        const unsigned long long quota = M - std::min(M, above);
-        unsigned long long *cnt = hist + kHistBins;
-        warm_assign_kernel<<<grid_for(n, 256), 256, 0, st>>>(T.ein, n, (uint32_t)thr, quota, T.map, T.owner, cnt);
-        fill_slots_kernel<<<grid_for(T.M * 32, 256), 256, 0, st>>>(reinterpret_cast<const uint8_t *>(h->b.vecs), pitch,
-                                                                   T.owner, T.M, T.cache);
-    }
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaStreamSynchronize(st));
+    rc = tier_init(h, tp, reinterpret_cast<const uint8_t *>(h->b.vecs), st);
+    if (rc) return rc;
     T.on = true;
-    unsigned long long s[kStWords];
-    CUDA_TRY(cudaMemcpy(s, h->status(), sizeof s, cudaMemcpyDeviceToHost));
-    T.last_hits = s[kStHits];
-    T.last_misses = T.misses_at_decay = s[kStMisses];
     return SVF_OK;
+}
+
+int svf_tier_reset(svf_index *h, const svf_tier_params *tp, void *stream) {
+    if (!h || !tp) return fail(SVF_EINVAL, "null arguments");
+    if (!h->tier.on) return fail(SVF_EINVAL, "the store is not tiered");
+    if (tp->M != h->tier.M) return fail(SVF_EINVAL, "reset keeps the cache size M");
+    svf_tier_sizes sz;
+    const int rc = svf_tier_buffer_sizes(&h->p, tp, &sz);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last = st;
+    return tier_init(h, tp, h->tier.host, st);
 }
 
 int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream) {
@@ -287,7 +320,10 @@ int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream) {
     unsigned long long s[kStWords];
     CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(cudaMemcpy(s, h->status(), sizeof s, cudaMemcpyDeviceToHost));
-    const int64_t c = (int64_t)std::min<unsigned long long>(s[kStQCount], T.qcap);
+    // STATIC keeps its cold-start cache (nothing is ever queued)
+    const int64_t c = T.policy == SVF_TIER_STATIC ? 0 : (int64_t)std::min<unsigned long long>(s[kStQCount], T.qcap);
+    const int by_order = T.policy == SVF_TIER_CLOCK;
+    const float wa = T.policy == SVF_TIER_WAVP ? T.alpha : 1.f, wb = T.policy == SVF_TIER_WAVP ? T.beta : 0.f;
     const unsigned long long prom0 = s[kStPromoted];
     float meanf = 0.f;
     const int64_t pitch = (int64_t)h->p.d * esize_of(h->p.dtype);
@@ -300,21 +336,22 @@ int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream) {
         const int64_t W = std::min<int64_t>((int64_t)T.sweep * B, T.M);
         const int64_t nw = pow2_at_least(W);
         CUDA_TRY(cudaMemsetAsync(fsum, 0, 4, st));
-        score_queue_kernel<<<grid_for(np, 256), 256, 0, st>>>(T.queue, c, np, T.freq, T.ein, T.alpha, T.beta, pk, fsum);
+        score_queue_kernel<<<grid_for(np, 256), 256, 0, st>>>(T.queue, c, np, T.freq, T.ein, wa, wb, by_order, pk,
+                                                               fsum);
         cudaFuncSetAttribute(sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxQueue * 8));
         sort_kernel<<<1, 1024, np * 8, st>>>(pk, (int)np);
         // the clock passes over the window; if too few slots were unreferenced
         // it comes round again (all reference bits are clear by then)
         unsigned long long *nvalid = reinterpret_cast<unsigned long long *>(fsum + 2);
         CUDA_TRY(cudaMemsetAsync(nvalid, 0, 8, st));
-        victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw, T.alpha,
-                                                          T.beta, vk, nvalid);
+        victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw, wa, wb,
+                                                          by_order, vk, nvalid);
         unsigned long long nv = 0;
         CUDA_TRY(cudaMemcpyAsync(&nv, nvalid, 8, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         if ((int64_t)nv < B)
             victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw,
-                                                              T.alpha, T.beta, vk, nvalid);
+                                                              wa, wb, by_order, vk, nvalid);
         sort_kernel<<<1, 1024, nw * 8, st>>>(vk, (int)nw);
         apply_kernel<<<grid_for(B * 32, 256), 256, 0, st>>>(pk, vk, B, T.map, T.owner, T.ref, T.host, T.cache, pitch,
                                                              h->status());
@@ -336,7 +373,7 @@ int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream) {
     // predicted access counts of the candidates both rose
     const double acc = (double)(s[kStHits] - T.last_hits) + (double)(s[kStMisses] - T.last_misses);
     const double rate = acc > 0 ? (double)(s[kStMisses] - T.last_misses) / acc : 0.0;
-    if (T.rounds > 0) {
+    if (T.rounds > 0 && T.policy == SVF_TIER_WAVP) {
         if (rate > T.last_rate && meanf > T.last_meanf)
             T.theta *= 1.25f;
         else

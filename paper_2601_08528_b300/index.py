@@ -162,11 +162,12 @@ class Index:
 
     # ------------------------------------------------------------ tiered store
     def enable_tier(self, M: int, qcap: int = 16384, promote_batch: int = 2048, sweep: int = 4, alpha: float = 0.6,
-                    beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16) -> None:
+                    beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp") -> None:
         """Move the primary rows to pinned host memory behind a device cache of
-        M rows with workload-aware placement (see svf_tier_enable)."""
+        M rows with workload-aware placement (see svf_tier_enable; policy:
+        wavp, clock, lfu or static)."""
         lib = L.load()
-        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every)
+        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every, L.TIER_POLICIES[policy], 0)
         sz = L.TierSizes()
         L.check(lib.svf_tier_buffer_sizes(C.byref(self.params), C.byref(tp), C.byref(sz)))
         u8 = torch.uint8
@@ -177,6 +178,14 @@ class Index:
                                                                       "queue", "scratch")],
                            self.host_store.data_ptr())
         L.check(lib.svf_tier_enable(self._h, C.byref(tp), C.byref(tb), _stream()))
+        torch.cuda.synchronize(self.device)
+
+    def reset_tier(self, M: int, qcap: int = 16384, promote_batch: int = 2048, sweep: int = 4, alpha: float = 0.6,
+                   beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp") -> None:
+        """Re-initialise the tiered store with new placement parameters (see
+        svf_tier_reset); M must stay the same."""
+        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every, L.TIER_POLICIES[policy], 0)
+        L.check(L.load().svf_tier_reset(self._h, C.byref(tp), _stream()))
         torch.cuda.synchronize(self.device)
 
     def release_device_store(self) -> None:

@@ -244,3 +244,94 @@ def test_tiered_lowp_rerank_equals_device(svf):
         b.insert(xi)
         b.maintain()
     assert torch.equal(a.vecs_fp8[:5000 * 128], b.vecs_fp8[:5000 * 128])
+
+
+# ---------------------------------------------------------------- placement-policy ablations
+def _clock_round(map_, owner, ref, queue, B, hand, W):
+    """CLOCK (recency only): the first B queued ids in queue order go into
+    the unreferenced slots the clock meets first (empty slots before owned
+    ones); referenced slots lose their bit; a second pass over the window
+    when too few were unreferenced."""
+    M = len(owner)
+    B, W = min(B, len(queue)), min(W, M)
+
+    def collect():
+        keys = []
+        for i in range(W):
+            s = (hand + i) % M
+            if ref[s]:
+                ref[s] = 0
+                continue
+            keys.append((0 if owner[s] < 0 else i + 1, s))
+        return keys
+
+    keys = collect()
+    if len(keys) < B:
+        keys = collect()
+    victims = [s for _, s in sorted(keys)][:B]
+    for x, s in zip(queue[:B], victims):
+        if owner[s] >= 0:
+            map_[owner[s]] = -1
+        owner[s], map_[x], ref[s] = x, s, 1
+    return min(B, len(victims))
+
+
+@pytest.mark.parametrize("policy", ["clock", "lfu", "static"])
+def test_policy_round(svf, orc, policy):
+    n, M, B = 4000, 256, 64
+    X, ix = built(svf, "u8", n, n, R=32)
+    ix.enable_tier(M=M, theta0=1e9, promote_batch=B, sweep=4, qcap=1024)
+    ix.reset_tier(M=M, theta0=1e9, promote_batch=B, sweep=4, qcap=1024, policy=policy)  # re-tier under the policy
+    rng = np.random.default_rng(731)
+    owner = np.full(M, -1, np.int32)
+    cached = rng.choice(n, 220, replace=False)
+    slots = rng.choice(M, 220, replace=False)
+    owner[slots] = cached
+    map_ = np.full(n, -1, np.int32)
+    map_[cached] = slots
+    ref = (rng.random(M) < 0.4).astype(np.uint8)
+    freq = rng.permutation(n).astype(np.uint32)
+    ein = rng.integers(0, 60, n).astype(np.uint32)  # ignored by clock and lfu
+    queue = rng.choice(np.setdiff1d(np.arange(n), cached), 150, replace=False).astype(np.uint32)
+    tb = ix.tier_bufs
+    tb["owner"][:M * 4].view(torch.int32).copy_(torch.from_numpy(owner))
+    tb["map"][:n * 4].view(torch.int32).copy_(torch.from_numpy(map_))
+    tb["ref"][:M].copy_(torch.from_numpy(ref))
+    fq = freq.copy()
+    fq[queue] |= np.uint32(1 << 31)
+    tb["freq"][:n * 4].view(torch.int32).copy_(torch.from_numpy(fq.view(np.int32)))
+    tb["ein"][:n * 4].view(torch.int32).copy_(torch.from_numpy(ein.view(np.int32)))
+    tb["queue"][:150 * 4].view(torch.int32).copy_(torch.from_numpy(queue.view(np.int32)))
+    ix.status.view(torch.int64)[11] = 150
+    torch.cuda.synchronize()
+    got = ix.maintain()
+    if policy == "static":
+        want = 0
+    elif policy == "lfu":
+        want, _ = orc.wavp_round(map_, owner, ref, freq, ein, queue, B, 0, 4 * B, 1.0, 0.0)  # F_recent alone
+    else:
+        want = _clock_round(map_, owner, ref, queue, B, 0, 4 * B)
+    assert got == want
+    np.testing.assert_array_equal(tb["owner"][:M * 4].view(torch.int32).cpu().numpy(), owner)
+    np.testing.assert_array_equal(tb["map"][:n * 4].view(torch.int32).cpu().numpy(), map_)
+    np.testing.assert_array_equal(tb["ref"][:M].cpu().numpy(), ref)
+    cache = tb["cache"][:M * 128].view(M, 128).cpu().numpy()
+    for s in np.where(np.isin(owner, queue))[0]:
+        np.testing.assert_array_equal(cache[s], X[owner[s]])
+
+
+@pytest.mark.parametrize("policy,queued", [("clock", True), ("static", False), ("wavp", False)])
+def test_policy_admission_on_misses(svf, policy, queued):
+    """With a threshold no miss reaches, WAVP queues nothing; CLOCK queues every
+    missed row regardless; STATIC never queues.  Results stay those of the
+    untiered store."""
+    X, ix = built(svf, "u8", 6000, 6000, R=32)
+    Q = torch.from_numpy(synth.sample("u8", 300, 741)).cuda()
+    cfg = svf.SearchConfig(k=10, L=64, T=32, seed=3)
+    ia, da = ix.search(Q, cfg)
+    ix.enable_tier(M=500, theta0=1e9, promote_batch=256, sweep=4, qcap=4096, policy=policy)
+    ib, db = ix.search(Q, cfg)
+    torch.cuda.synchronize()
+    assert torch.equal(ia, ib) and torch.equal(da, db)
+    assert ix.stats()["cache_misses"] > 0
+    assert (int(ix.status.view(torch.int64)[11]) > 0) == queued
