@@ -439,8 +439,8 @@ def main():
     torch.cuda.synchronize()
     log_t("ground truth")
 
-    grid = [(64, 32), (64, 64), (64, 96), (128, 48), (128, 56), (128, 64), (128, 72), (128, 80), (128, 96),
-            (256, 96), (256, 128)]
+    grid = [(64, 32), (64, 64), (64, 72), (64, 80), (64, 96), (128, 48), (128, 56), (128, 64), (128, 72), (128, 80),
+            (128, 96), (256, 96), (256, 128)]
     if a.impl == "reference":
         # the oracle on the plain form's operating point
         base = [("fp32", svf.SearchConfig(k=K))]
