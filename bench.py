@@ -147,6 +147,24 @@ STOP_EVERY = 4
 METRIC = "search QPS at recall@10>=0.95 (plain FP32 vs BF16/FP8 + learned stop)"
 
 
+def max_over_ranks(x, dist):
+    """Max over ranks of a host float: every rank's timed region ends when the
+    slowest does (NCCL reduces a device tensor, gloo a host one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the max-over-
+    ranks time (weak scaling: every rank has its own batch)."""
+    return world * units_per_rank / seconds
+
+
 def unit96_name(n):
     return f"unit96-{n // 1_000_000}M" if n % 1_000_000 == 0 else f"unit96-{n}"
 
@@ -509,11 +527,7 @@ def main():
     if dist:
         dist.barrier()
     per = [e0.elapsed_time(e1) / 1e3 for e0, e1 in evs]
-    total = sum(per)
-    if dist:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(sum(per), dist)
     s = ix.stats()
     # ---- end to end: pinned host queries in, results out, every step
     Qh = torch.from_numpy(Qe_np).pin_memory()
@@ -529,6 +543,8 @@ def main():
     ev = lambda: torch.cuda.Event()
     up, srch = [ev(), ev()], [ev(), ev()]
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     cs.wait_event(e0)
@@ -552,7 +568,7 @@ def main():
     st.wait_stream(cs)
     e1.record(st)
     e1.synchronize()
-    e2e_t = e0.elapsed_time(e1) / 1e3
+    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
     clk = clocks.stop(torch.cuda.current_device())
 
     # ---- roofline of the search kernel (the only launch of a step)
@@ -568,7 +584,7 @@ def main():
     achieved = alg / mean_launch / 1e9
     out = {
         "metric": METRIC,
-        "value": world * nq * a.steps / total,
+        "value": job_rate(nq * a.steps, world, total),
         "unit": "queries/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": form.split("+")[0],
@@ -584,7 +600,7 @@ def main():
                      "peak_source": src,
                      "alg_bytes_per_launch": alg, "iters_per_launch": iters, "evals_per_launch": evals,
                      "hash_resets": s["hash_resets"]},
-        "e2e": {"value": world * nq * a.steps / e2e_t, "unit": "queries/s",
+        "e2e": {"value": job_rate(nq * a.steps, world, e2e_t), "unit": "queries/s",
                 "h2d_bytes_per_step": Qh.numel() * 4, "d2h_bytes_per_step": ids_h.numel() * 4 + d_h.numel() * 4},
         "gpu_launches": a.steps,
         "clocks": clk,
