@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         np = min(np + nf, L);
         ran = t + 1;
 
-        if (learn) {
+        if constexpr (LEARN) {
             // newtop: entries of the new top-k admitted in this iteration (an
             // older entry can only move down, so these are exactly the new ids)
             const int kk = min(a.k, np);

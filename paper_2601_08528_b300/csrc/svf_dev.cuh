@@ -706,47 +706,48 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
                     if (vb) keys[i0 + rb] = make_key(finish_key<DT>(R.metric, fb, ib, sb), list[i0 + rb] | flags);
                 }
             }
-            continue;
-        }
-        for (int r0 = 0; r0 < cnt; r0 += nteam) {
-            if (r0 == h) {  // the second half
-                uint32_t it = 0;
-                while (!mbar_try_wait(S.mbar + 1, S.phase[1]))
-                    if (++it > kWaitLimit) return false;
-                S.phase[1] ^= 1u;
-            }
-            const int r = r0 + team;
-            const bool valid = r < cnt;
-            const uint8_t *row = S.buf + (size_t)(valid ? r : 0) * cb;
-            float facc = 0.f, scale = 1.f;
-            uint32_t iacc = 0;
-            uint64_t pacc[2] = {0, 0};
-            if (DT == SVF_FP8) scale = *reinterpret_cast<const float *>(row + R.d);
-            constexpr int MC = max_chunks_per_lane(DT);
-            uint4 v[MC];
+        } else {
+            for (int r0 = 0; r0 < cnt; r0 += nteam) {
+                if (r0 == h) {  // the second half
+                    uint32_t it = 0;
+                    while (!mbar_try_wait(S.mbar + 1, S.phase[1]))
+                        if (++it > kWaitLimit) return false;
+                    S.phase[1] ^= 1u;
+                }
+                const int r = r0 + team;
+                const bool valid = r < cnt;
+                const uint8_t *row = S.buf + (size_t)(valid ? r : 0) * cb;
+                float facc = 0.f, scale = 1.f;
+                uint32_t iacc = 0;
+                uint64_t pacc[2] = {0, 0};
+                if (DT == SVF_FP8) scale = *reinterpret_cast<const float *>(row + R.d);
+                constexpr int MC = max_chunks_per_lane(DT);
+                uint4 v[MC];
 #pragma unroll
-            for (int u = 0; u < MC; u++) {
-                const int c = sub + u * ts;
-                if (valid && u < cpl && c < nch) v[u] = reinterpret_cast<const uint4 *>(row)[c];
-            }
+                for (int u = 0; u < MC; u++) {
+                    const int c = sub + u * ts;
+                    if (valid && u < cpl && c < nch) v[u] = reinterpret_cast<const uint4 *>(row)[c];
+                }
 #pragma unroll
-            for (int u = 0; u < MC; u++) {
-                const int c = sub + u * ts;
-                if (valid && u < cpl && c < nch)
-                    chunk_acc<DT>(R.metric, v[u], c, qf, qb, scale, facc, iacc, pacc);
+                for (int u = 0; u < MC; u++) {
+                    const int c = sub + u * ts;
+                    if (valid && u < cpl && c < nch)
+                        chunk_acc<DT>(R.metric, v[u], c, qf, qb, scale, facc, iacc, pacc);
+                }
+                for (int c0 = sub + MC * ts; c0 < nch; c0 += ts)  // rows longer than MC chunks per lane
+                    if (valid)
+                        chunk_acc<DT>(R.metric, reinterpret_cast<const uint4 *>(row)[c0], c0, qf, qb, scale, facc, iacc,
+                                      pacc);
+                fold_pacc<DT>(facc, pacc);
+                for (int m = ts >> 1; m > 0; m >>= 1) {
+                    if constexpr (DT == SVF_U8)
+                        iacc += __shfl_xor_sync(kFull, iacc, m);
+                    else
+                        facc += __shfl_xor_sync(kFull, facc, m);
+                }
+                if (valid && sub == 0)
+                    keys[i0 + r] = make_key(finish_key<DT>(R.metric, facc, iacc, scale), list[i0 + r] | flags);
             }
-            for (int c0 = sub + MC * ts; c0 < nch; c0 += ts)  // rows longer than MC chunks per lane
-                if (valid)
-                    chunk_acc<DT>(R.metric, reinterpret_cast<const uint4 *>(row)[c0], c0, qf, qb, scale, facc, iacc,
-                                  pacc);
-            fold_pacc<DT>(facc, pacc);
-            for (int m = ts >> 1; m > 0; m >>= 1) {
-                if constexpr (DT == SVF_U8)
-                    iacc += __shfl_xor_sync(kFull, iacc, m);
-                else
-                    facc += __shfl_xor_sync(kFull, facc, m);
-            }
-            if (valid && sub == 0) keys[i0 + r] = make_key(finish_key<DT>(R.metric, facc, iacc, scale), list[i0 + r] | flags);
         }
     }
     __syncwarp();
