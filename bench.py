@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--serve-policies", default="",
                     help="comma list of extra cache placement policies (clock,lfu,static) run on the same serving "
                          "stream after WAVP, for the ablation")
+    ap.add_argument("--serve-trav", default="fp8", choices=["fp8", "fp32"],
+                    help="unit96-10M serving stream: the measured fp8 form (traversal resident, re-rank rows "
+                         "through the tier), or plain fp32 (every traversal row through the tier)")
     ap.add_argument("--serve-lins", type=int, default=128, help="insert search pool of the 50M build")
     ap.add_argument("--serve-tins", type=int, default=96, help="insert search iterations of the 50M build")
     return ap.parse_args()
@@ -613,10 +616,15 @@ def main():
         tier = dict(M=int(a.n * 0.3125), theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
         ix.enable_tier(**tier)
         X_ins = synth.sample_chunked("unit96", 200_000, 305)
+        if a.serve_trav == "fp32":
+            fp = best.get("fp32", {"L": 64, "T": 96})
+            cfg = svf.SearchConfig(k=K, L=fp["L"], T=fp["T"])
+            trav = "fp32 traversal through the tier"
+        else:
+            trav = "fp8 traversal + exact re-rank"
         out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg)
         out["serving"]["workload"] = ("unit96-10M tiered: fp32 rows in pinned host memory behind a 3.1M-row device "
-                                      "cache, fp8 traversal + exact re-rank, Zipf(1.1) queries, 90:9:1 mix, "
-                                      "batches log-uniform 1..2048")
+                                      f"cache, {trav}, Zipf(1.1) queries, 90:9:1 mix, batches log-uniform 1..2048")
         out["serving"]["policy"] = "wavp"
         log_t("serving", json.dumps(out["serving"]))
         # placement ablation: the same stream (same seed) after re-tiering the
