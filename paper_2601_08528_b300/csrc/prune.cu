@@ -153,7 +153,8 @@ cudaError_t launch_prune(const PruneArgs &a, int max_lists, cudaStream_t st) {
     const int m = a.cand_stride;
     bool stage = a.mode == SVF_PRUNE_RNG && (size_t)m * a.X.nchunk * 16 <= 160 * 1024;
     size_t smem = prune_smem(a.X.nchunk, false) + (stage ? (size_t)m * a.X.nchunk * 16 : 0);
-    int grid = max_lists < 148 * 64 ? max_lists : 148 * 64;
+    const int cap = sm_count() * 64;
+    int grid = max_lists < cap ? max_lists : cap;
     if (a.X.dtype == SVF_U8) {
         cudaFuncSetAttribute(prune_kernel<SVF_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         prune_kernel<SVF_U8><<<grid, THREADS, smem, st>>>(a, stage ? 1 : 0);

@@ -9,6 +9,18 @@
 
 namespace svf {
 
+// SMs of the current device (148 on a B300 when no device can be queried,
+// e.g. sizing scratch on a host without a GPU).
+inline int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0) {
+        cudaGetLastError();
+        return 148;
+    }
+    return n;
+}
+
 constexpr int kSearchWarps = 4;  // queries (warps) per CTA
 
 struct SearchArgs {

@@ -540,11 +540,11 @@ bool make_map(CUtensorMap *m, void *base, int64_t rows, int kp, int box_rows) {
 }
 
 // Database slices per query tile: one CTA per SM, so the grid (query
-// tiles x slices) should fill whole waves of the 148 SMs.  Take the
+// tiles x slices) should fill whole waves of the SMs.  Take the
 // smallest count that fills at least one wave with >= 95% of the last
 // wave busy, else the best fill up to 64 slices.
 int split_count(int64_t n, int64_t nq) {
-    constexpr int kSMs = 148;
+    const int kSMs = sm_count();
     const int64_t qt = (nq + TM - 1) / TM;
     const int64_t max_s = std::min<int64_t>(64, (n + TN - 1) / TN);
     int64_t best = 1;

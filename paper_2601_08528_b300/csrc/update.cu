@@ -275,7 +275,8 @@ cudaError_t launch_delete_mark(const uint32_t *ids, int64_t m, int64_t n_used, u
 cudaError_t launch_delete_scan(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, uint32_t *vl,
                                unsigned long long *status, cudaStream_t st) {
     if (n_used == 0) return cudaSuccess;
-    int64_t warps = n_used < 148LL * 64 ? n_used : 148LL * 64;
+    const int64_t cap = (int64_t)sm_count() * 64;
+    int64_t warps = n_used < cap ? n_used : cap;
     del_scan_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(graph, R, del, n_used, vl, status);
     return cudaGetLastError();
 }
