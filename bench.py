@@ -67,6 +67,11 @@ def parse():
     ap.add_argument("--serve-policies", default="",
                     help="comma list of extra cache placement policies (clock,lfu,static) run on the same serving "
                          "stream after WAVP, for the ablation")
+    ap.add_argument("--serve-window", default="",
+                    help="W,speed: queries from a sliding window of W components moving `speed` components/s "
+                         "(default: Zipf(1.1) over all components)")
+    ap.add_argument("--serve-cache-frac", type=float, default=0.3125, help="device cache rows / n (unit96-10M)")
+    ap.add_argument("--serve-maintain-every", type=int, default=128, help="search batches between maintenance")
     ap.add_argument("--serve-trav", default="fp8", choices=["fp8", "fp32"],
                     help="unit96-10M serving stream: the measured fp8 form (traversal resident, re-rank rows "
                          "through the tier), or plain fp32 (every traversal row through the tier)")
@@ -208,7 +213,7 @@ def train_stops(torch, svf, ix, Qtr, gt_cal, ncal, precisions):
 
 # ---------------------------------------------------------------- serving
 def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zipf_s=1.1, max_inflight=8,
-                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048):
+                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048, window=None):
     """Open-loop Poisson stream at `rate` requests/s for `duration` s through
     the continuous-batching server: 90:9:1 search:insert:delete requests,
     batch sizes floor(exp(U[0, ln max_batch])), query components ~ Zipf(s).
@@ -227,9 +232,19 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
         ops.append(0 if u < 0.90 else (1 if u < 0.99 else 2))
         sizes.append(max(1, min(max_batch, int(np.exp(rng.uniform(0, np.log(max_batch)))))))
     nq = sum(sz for o, sz in zip(ops, sizes) if o == 0)
-    Qall = torch.from_numpy(synth.sample_chunked(m, max(nq, 1), seed + 1,
-                                                 component_sampler=synth.zipf_components(m.n_centres, zipf_s,
-                                                                                          seed + 2))).cuda()
+    if window:
+        # query components from a sliding window (width, components/s): the hot set moves
+        wdraw = synth.window_components(m.n_centres, window[0], window[1], seed + 2)
+        wrng = np.random.default_rng(seed + 3)
+        labels = np.concatenate([wdraw(wrng, ta, sz) for ta, o, sz in zip(arr, ops, sizes) if o == 0] or
+                                [np.zeros(1, np.int64)])
+        Qall = torch.from_numpy(synth.sample_chunked(m, max(nq, 1), seed + 1,
+                                                     component_sampler=synth.given_components(labels),
+                                                     workers=1)).cuda()
+    else:
+        Qall = torch.from_numpy(synth.sample_chunked(m, max(nq, 1), seed + 1,
+                                                     component_sampler=synth.zipf_components(m.n_centres, zipf_s,
+                                                                                              seed + 2))).cuda()
     k = cfg.k
     ids_out = torch.empty((max(nq, 1), k), dtype=torch.int32, device="cuda")
     d_out = torch.empty((max(nq, 1), k), dtype=torch.int32 if m.dtype == "u8" else torch.float32, device="cuda")
@@ -613,7 +628,11 @@ def main():
     # fp8 traversal resident, exact re-rank through the tier; an open-loop
     # Poisson stream of uneven batches with inserts and deletes
     if a.serve_rate > 0:
-        tier = dict(M=int(a.n * 0.3125), theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
+        tier = dict(M=int(a.n * a.serve_cache_frac), theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
+        win_arg = tuple(float(x) for x in a.serve_window.split(",")) if a.serve_window else None
+        if win_arg:
+            win_arg = (int(win_arg[0]), win_arg[1])
+        sopt = dict(maintain_every=a.serve_maintain_every, window=win_arg)
         ix.enable_tier(**tier)
         X_ins = synth.sample_chunked("unit96", 200_000, 305)
         if a.serve_trav == "fp32":
@@ -622,9 +641,13 @@ def main():
             trav = "fp32 traversal through the tier"
         else:
             trav = "fp8 traversal + exact re-rank"
-        out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg)
-        out["serving"]["workload"] = ("unit96-10M tiered: fp32 rows in pinned host memory behind a 3.1M-row device "
-                                      f"cache, {trav}, Zipf(1.1) queries, 90:9:1 mix, batches log-uniform 1..2048")
+        out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg,
+                                      **sopt)
+        qmix = (f"queries from a window of {win_arg[0]} components moving {win_arg[1]:g}/s" if win_arg
+                else "Zipf(1.1) queries")
+        out["serving"]["workload"] = (f"unit96-10M tiered: fp32 rows in pinned host memory behind a "
+                                      f"{tier['M'] / 1e6:.1f}M-row device cache, {trav}, {qmix}, 90:9:1 mix, "
+                                      "batches log-uniform 1..2048")
         out["serving"]["policy"] = "wavp"
         log_t("serving", json.dumps(out["serving"]))
         # placement ablation: the same stream (same seed) after re-tiering the
@@ -633,7 +656,8 @@ def main():
             out["serving_policies"] = {"wavp": out["serving"]}
             for p in policies:
                 ix.reset_tier(policy=p, **tier)
-                r = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg)
+                r = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg,
+                                 **sopt)
                 r["policy"] = p
                 out["serving_policies"][p] = r
                 log_t("serving", p, json.dumps(r))

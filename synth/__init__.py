@@ -165,6 +165,30 @@ def pick_live_ids(n_used: int, deleted: np.ndarray | None, m: int, seed: int) ->
     return np.sort(rng.choice(live, size=min(m, live.size), replace=False)).astype(np.uint32)
 
 
+def given_components(labels: np.ndarray):
+    """Sampler that hands out the given component labels in order (use with
+    workers=1 so chunks are drawn in order)."""
+    pos = [0]
+
+    def draw(rng, m):
+        out = labels[pos[0]:pos[0] + m]
+        pos[0] += m
+        return out
+    return draw
+
+
+def window_components(n_components: int, width: int, speed: float, seed: int):
+    """Components of a sliding window: a query arriving at time t (s) draws
+    uniformly from `width` consecutive components (of a seeded permutation)
+    starting at floor(t * speed).  Returns f(rng, t, m)."""
+    perm = np.random.default_rng(seed).permutation(n_components)
+
+    def draw(rng, t, m):
+        start = int(np.floor(t * speed))
+        return perm[(start + rng.integers(0, width, m)) % n_components]
+    return draw
+
+
 def zipf_components(n_components: int, s: float, seed: int):
     """Sampler of mixture components ~ Zipf(s) over a seeded permutation."""
     perm = np.random.default_rng(seed).permutation(n_components)
