@@ -4,7 +4,7 @@ compute one at a time, and by properties that hold at any size.
 * unit96, 10M x 96 inner product, R = 32, built as the benchmark builds it
   (exact build of 200,000 rows, then inserts of the rest); 10,000 queries
   searched in the benchmark's launch configuration (L = 64, T = 96), plain
-  FP32 and FP8 traversal + exact FP32 re-rank; a sample of the queries is
+  FP32, and BF16 / FP8 traversal + exact FP32 re-rank; a sample of the queries is
   searched by the FP64 oracle on the same graph.
 * u8, 1M x 128 uint8 squared L2, R = 64: the GPU's exact build checked row
   by row on sampled vertices (exact 128-NN + prune by the oracle), sampled
@@ -34,7 +34,7 @@ def svf():
 @pytest.fixture(scope="module")
 def unit96(svf):
     X = synth.sample_chunked("unit96", N96, 300)
-    ix = svf.Index(96, N96, dtype="f32", metric="ip", R=32, lowp=("fp8",), max_batch=1_000_000)
+    ix = svf.Index(96, N96, dtype="f32", metric="ip", R=32, lowp=("bf16", "fp8"), max_batch=1_000_000)
     ix.build(torch.from_numpy(X[:200_000]).cuda())
     while ix.n_used < N96:
         b = min(ix.n_used, 1_000_000, N96 - ix.n_used)
@@ -77,15 +77,16 @@ def test_unit96_10M_fp32_search_sampled(svf, orc, unit96):
     P.check_fp32(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], o, X, Q[qs], "ip")
 
 
-def test_unit96_10M_fp8_rerank_search_sampled(svf, orc, unit96):
+@pytest.mark.parametrize("prec", ["fp8", "bf16"])
+def test_unit96_10M_lowp_rerank_search_sampled(svf, orc, unit96, prec):
     X, ix, g, Q = unit96
     L = 64
     ids, dist = ix.search(torch.from_numpy(Q).cuda(),
-                          svf.SearchConfig(k=10, L=L, T=96, precision="fp8", rerank=True, seed=SEED))
+                          svf.SearchConfig(k=10, L=L, T=96, precision=prec, rerank=True, seed=SEED))
     qs = sample(NQ, 48, 12)
-    lst = orc.Store.from_vectors(X, "ip", dtype="fp8")
+    lst = orc.Store.from_vectors(X, "ip", dtype=prec)
     o = orc.search(lst, N96, g, None, Q[qs], 10, L, 96, SEED, want_pool=True)
-    # oracle: exact FP64 distances of the final fp8-traversal pool, re-sorted by (dist, id)
+    # oracle: exact FP64 distances of the final low-precision-traversal pool, re-sorted by (dist, id)
     st = orc.Store.from_vectors(X, "ip")
     pd = orc.dist_ids(st, Q[qs], o["pool_ids"])
     want_i = np.empty((len(qs), 10), np.int64)
