@@ -64,7 +64,7 @@ def lib():
             "orc_knn": (None, [S, P, P, I64, P, I32, P, P, P]),
             "orc_prune": (D, [S, P, P, P, I32, I32, P, I32, I32, P]),
             "orc_build": (None, [S, I32, I32, P, P]),
-            "orc_search": (None, [S, I64, P, I32, P, P, I64, P, I32, I32, I32, U64, P, P, P, P, P, P, P]),
+            "orc_search": (I32, [S, I64, P, I32, P, P, I64, P, I32, I32, I32, U64, I32, P, P, P, P, P, P, P]),
             "orc_insert": (None, [S, I64, I64, P, I32, P, I32, I32, U64, I32, P, P]),
             "orc_delete": (I64, [S, I64, P, I32, P, P, I64, I32, I32, P, P]),
             "orc_threads": (I32, []),
@@ -214,8 +214,10 @@ def build_graph(store: Store, R: int, mode: int = PRUNE_RNG):
 
 
 def search(store: Store, n_used: int, graph: np.ndarray, delbits: np.ndarray | None, Q: np.ndarray, k: int,
-           L: int, T: int, seed: int, qkeys: np.ndarray | None = None, want_pool: bool = False):
-    """Algorithm 1 with fixed T.  Returns a dict of numpy arrays."""
+           L: int, T: int, seed: int, qkeys: np.ndarray | None = None, want_pool: bool = False, W: int = 1):
+    """Algorithm 1 with fixed T; W > 1 expands the W nearest unexpanded pool
+    entries per iteration (iters counts parents).  Returns a dict of numpy
+    arrays."""
     Q = np.ascontiguousarray(Q)
     nq = Q.shape[0]
     R = graph.shape[1]
@@ -232,9 +234,11 @@ def search(store: Store, n_used: int, graph: np.ndarray, delbits: np.ndarray | N
         out["pool_dist"] = np.zeros((nq, L), dtype=np.float64)
     qk = None if qkeys is None else np.ascontiguousarray(qkeys, dtype=np.uint64)
     st = store.c()
-    lib().orc_search(C.byref(st), n_used, _p(graph), R, _p(delbits), _p(Q), nq, _p(qk), k, L, T, seed,
-                     _p(out["ids"]), _p(out["dist"]), _p(out["gap"]), _p(out["iters"]), _p(out["evals"]),
-                     _p(out.get("pool_ids")), _p(out.get("pool_dist")))
+    rc = lib().orc_search(C.byref(st), n_used, _p(graph), R, _p(delbits), _p(Q), nq, _p(qk), k, L, T, seed, W,
+                          _p(out["ids"]), _p(out["dist"]), _p(out["gap"]), _p(out["iters"]), _p(out["evals"]),
+                          _p(out.get("pool_ids")), _p(out.get("pool_dist")))
+    if rc != 0:
+        raise ValueError(f"W = {W} out of range")
     return out
 
 

@@ -57,6 +57,7 @@
 #endif
 
 #define ORC_EMPTY 0xFFFFFFFFu
+#define ORC_MAX_W 32 /* most parents per iteration */
 
 enum { ORC_F32 = 0, ORC_U8 = 1, ORC_BF16 = 2, ORC_FP8 = 3 };
 enum { ORC_L2 = 0, ORC_IP = 1 };
@@ -540,6 +541,7 @@ typedef struct {
     const uint32_t *del;
     int32_t L, T, k;
     uint64_t seed;
+    int32_t W;  /* parents expanded per iteration (0 or 1: Alg. 1 as printed) */
 } srch_ctx;
 
 typedef struct {
@@ -626,34 +628,42 @@ static double search_one(const orc_store *X, const srch_ctx *S, const double *q,
         F->stop_iter = -1;
     }
 
+    const int W = S->W > 1 ? S->W : 1;
     for (int t = 0; t < S->T; t++) {
-        int p = -1, p2 = -1;
+        /* GetNearest, widened to the W nearest unexpanded entries (W = 1 is
+           Alg. 1): par[] lists them in (dist, id) order; pn is the next
+           unexpanded entry, which decides the last parent against it. */
+        int par[ORC_MAX_W], npar = 0, pn = -1;
         for (int i = 0; i < np; i++)
             if (!pool[i].exp) {
-                if (p < 0) p = i;
-                else { p2 = i; break; }
+                if (npar < W) par[npar++] = i;
+                else { pn = i; break; }
             }
-        if (p < 0) break; /* nothing left to expand: the pool stays unchanged */
-        if (p2 >= 0) {
-            double gi = rel_gap(pool[p].d, pool[p].s, pool[p2].d, pool[p2].s);
+        if (npar == 0) break; /* nothing left to expand: the pool stays unchanged */
+        int p = par[0];
+        if (pn >= 0) {
+            double gi = rel_gap(pool[par[npar - 1]].d, pool[par[npar - 1]].s, pool[pn].d, pool[pn].s);
             if (gi < gap) gap = gi;
         }
-        pool[p].exp = 1;
-        st->iters++;
-        const uint32_t *row = S->graph + (int64_t)pool[p].id * R;
+        for (int j = 0; j < npar; j++) pool[par[j]].exp = 1;
+        st->iters += npar;
         int nb = np;
         memcpy(buf, pool, sizeof(ent) * np);
-        for (int r = 0; r < R; r++) {
-            uint32_t v = row[r];
-            if (v == ORC_EMPTY || (int64_t)v >= S->n_used) continue;
-            if (is_deleted(S->del, v) || set_has(&vis, v)) continue;
-            set_add(&vis, v);
-            decode_row(X, v, x);
-            buf[nb].d = vdist(q, x, d, X->metric, &buf[nb].s);
-            buf[nb].id = v;
-            buf[nb].exp = 0;
-            nb++;
-            st->evals++;
+        /* the parents' rows in turn; an id named by two parents is visited once */
+        for (int j = 0; j < npar; j++) {
+            const uint32_t *row = S->graph + (int64_t)pool[par[j]].id * R;
+            for (int r = 0; r < R; r++) {
+                uint32_t v = row[r];
+                if (v == ORC_EMPTY || (int64_t)v >= S->n_used) continue;
+                if (is_deleted(S->del, v) || set_has(&vis, v)) continue;
+                set_add(&vis, v);
+                decode_row(X, v, x);
+                buf[nb].d = vdist(q, x, d, X->metric, &buf[nb].s);
+                buf[nb].id = v;
+                buf[nb].exp = 0;
+                nb++;
+                st->evals++;
+            }
         }
         int k = S->k;
         int kk_prev = np < k ? np : k;
@@ -737,22 +747,25 @@ static double search_one(const orc_store *X, const srch_ctx *S, const double *q,
     return gap;
 }
 
-/* Batched search.  Outputs (each optional except ids):
-     out_ids/out_d [nq][k]  (EMPTY / +inf pad), out_gap[nq], out_iters[nq],
-     out_evals[nq], pool_ids/pool_d [nq][L] (the final pool, EMPTY / +inf pad). */
-void orc_search(const orc_store *X, int64_t n_used, const uint32_t *graph, int32_t R, const uint32_t *del,
-                const void *Q, int64_t nq, const uint64_t *qkeys, int32_t k, int32_t L, int32_t T, uint64_t seed,
-                uint32_t *out_ids, double *out_d, double *out_gap, int32_t *out_iters, int64_t *out_evals,
-                uint32_t *pool_ids, double *pool_d) {
-    srch_ctx S = {n_used, graph, R, del, L, T, k, seed};
+/* Batched search, W parents per iteration (1 <= W <= ORC_MAX_W; W = 1 is
+   Alg. 1).  Outputs (each optional except ids):
+     out_ids/out_d [nq][k]  (EMPTY / +inf pad), out_gap[nq], out_iters[nq]
+     (parents expanded), out_evals[nq], pool_ids/pool_d [nq][L] (the final
+     pool, EMPTY / +inf pad).  Returns -1 for W out of range. */
+int orc_search(const orc_store *X, int64_t n_used, const uint32_t *graph, int32_t R, const uint32_t *del,
+               const void *Q, int64_t nq, const uint64_t *qkeys, int32_t k, int32_t L, int32_t T, uint64_t seed,
+               int32_t W, uint32_t *out_ids, double *out_d, double *out_gap, int32_t *out_iters, int64_t *out_evals,
+               uint32_t *pool_ids, double *pool_d) {
+    if (W < 1 || W > ORC_MAX_W) return -1;
+    srch_ctx S = {n_used, graph, R, del, L, T, k, seed, W};
     int d = X->d;
     int64_t qb = query_bytes(X);
 #pragma omp parallel
     {
         double *q = (double *)malloc(sizeof(double) * d);
         double *x = (double *)malloc(sizeof(double) * d);
-        ent *pool = (ent *)malloc(sizeof(ent) * (L + R + 1));
-        ent *buf = (ent *)malloc(sizeof(ent) * (L + R + 1));
+        ent *pool = (ent *)malloc(sizeof(ent) * (L + (size_t)W * R + 1));
+        ent *buf = (ent *)malloc(sizeof(ent) * (L + (size_t)W * R + 1));
 #pragma omp for schedule(dynamic, 1)
         for (int64_t qi = 0; qi < nq; qi++) {
             decode_query(X, Q, qi, q);
@@ -778,6 +791,7 @@ void orc_search(const orc_store *X, int64_t n_used, const uint32_t *graph, int32
         free(pool);
         free(buf);
     }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

@@ -288,6 +288,58 @@ def test_search_tiny_n_pads(orc):
     assert sorted(r["ids"][0, :5].tolist()) == [0, 1, 2, 3, 4]
 
 
+def test_search_w_parents_hand_worked(orc):
+    # W nearest unexpanded entries per iteration (Sec. 4.4 intra-query
+    # parallelism over Alg. 1): a hand-worked 12-point line graph
+    g = _golden("search_wparents_hand.json")
+    n, L = g["n"], g["L"]
+    X = np.zeros((n, 4), dtype=np.float32)
+    X[:, 0] = np.arange(n)
+    st = orc.Store.from_vectors(X, "l2")
+    graph = np.array(g["graph"], dtype=np.uint32)
+    q = np.array([g["query"]], dtype=np.float32)
+    r0 = orc.search(st, n, graph, None, q, L, L, 0, g["seed"], want_pool=True)
+    assert r0["pool_ids"][0].tolist() == g["init_pool"]
+    for c in g["cases"]:
+        r = orc.search(st, n, graph, None, q, L, L, c["T"], g["seed"], want_pool=True, W=c["W"])
+        assert r["pool_ids"][0].tolist() == c["pool"], c
+        assert (r["iters"][0], r["evals"][0]) == (c["parents"], c["evals"]), c
+        assert r["ids"][0].tolist() == c["pool"]
+
+
+@pytest.mark.parametrize("W", [2, 4, 8])
+def test_search_w_parents_beam_ge_n_is_exact_knn(orc, W):
+    n = 150
+    X = synth.sample("tiny", n, 31)
+    Q = synth.sample("tiny", 20, 32)
+    st = orc.Store.from_vectors(X, "l2")
+    g = _ring_graph(n, 4, 33)
+    r = orc.search(st, n, g, None, Q, 10, 256, 256, 1, W=W)
+    ni, nd = _np_knn(X, Q, 10, "l2")
+    np.testing.assert_array_equal(r["ids"], ni)
+    np.testing.assert_allclose(r["dist"], nd, rtol=1e-12, atol=1e-9)
+
+
+def test_search_w_parents_counts_and_range(orc):
+    # every iteration expands exactly W parents while the pool has that many
+    # unexpanded entries (a large graph and few iterations); W = 1 is Alg. 1
+    n = 3000
+    X = synth.sample("tiny", n, 81)
+    st = orc.Store.from_vectors(X, "l2")
+    g, _ = orc.build_graph(st, 16)
+    Q = synth.sample("tiny", 16, 82)
+    for W in (1, 2, 4):
+        r = orc.search(st, n, g, None, Q, 10, 64, 6, 5, W=W)
+        assert np.all(r["iters"] == 6 * W)
+        assert np.all(r["evals"] <= 64 + 6 * W * 16)
+    a = orc.search(st, n, g, None, Q, 10, 64, 20, 5)
+    b = orc.search(st, n, g, None, Q, 10, 64, 20, 5, W=1)
+    np.testing.assert_array_equal(a["ids"], b["ids"])
+    for W in (0, 33):
+        with pytest.raises(ValueError):
+            orc.search(st, n, g, None, Q, 10, 64, 4, 5, W=W)
+
+
 # ---------------------------------------------------------------- insert (Sec. 5.1)
 def test_insert_invariants_and_read_after_write(orc):
     n0, m, R = 1500, 200, 16
