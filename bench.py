@@ -75,6 +75,11 @@ def parse():
     ap.add_argument("--serve-trav", default="fp8", choices=["fp8", "fp32"],
                     help="unit96-10M serving stream: the measured fp8 form (traversal resident, re-rank rows "
                          "through the tier), or plain fp32 (every traversal row through the tier)")
+    ap.add_argument("--serve-small", type=int, default=16,
+                    help="serve128-50M: search batches of at most this many queries run with 8 warps per query "
+                         "(0: one warp per query throughout)")
+    ap.add_argument("--serve-compare", action="store_true",
+                    help="serve128-50M: also run each rate's stream with one warp per query throughout")
     ap.add_argument("--serve-lins", type=int, default=128, help="insert search pool of the 50M build")
     ap.add_argument("--serve-tins", type=int, default=96, help="insert search iterations of the 50M build")
     return ap.parse_args()
@@ -155,6 +160,43 @@ STOP_EVERY = 4
 METRIC = "search QPS at recall@10>=0.95 (plain FP32 vs BF16/FP8 + learned stop)"
 
 
+def small_batch(svf, torch, ix, Q, gt, cfg, target, Ws=(1, 2, 4, 8), sizes=(1, 16), reps=200):
+    """Several warps per query (W parents per iteration) for latency-bound
+    batches: for each W the cheapest swept T whose recall@10 over all queries
+    reaches `target`, then the latency of batches of 1 and 16 queries through
+    the public API (CUDA events around the call, host overhead included)."""
+    out = {}
+    for W in Ws:
+        Ts = sorted({max(2, int(np.ceil(cfg.T * f / W))) for f in (0.8, 1.0, 1.25, 1.5, 2.0)})
+        pick = None
+        for T in Ts:
+            c = dataclasses.replace(cfg, T=T, W=W, mlp=None)
+            ids, _ = ix.search(Q, c)
+            r = (ids.long().unsqueeze(2) == gt.long().unsqueeze(1)).any(2).float().mean().item()
+            if r >= target:
+                pick = (c, r)
+                break
+        if pick is None:
+            continue
+        c, r = pick
+        row = {"T": c.T, "recall@10": r}
+        for b in sizes:
+            ts = []
+            for i in range(reps):
+                q = Q[(i * b) % (Q.shape[0] - b):][:b]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ix.search(q, c)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            row[f"b{b}_p50_ms"] = float(np.percentile(ts, 50))
+            row[f"b{b}_p99_ms"] = float(np.percentile(ts, 99))
+        row["cfg"] = c
+        out[W] = row
+    return out
+
+
 def max_over_ranks(x, dist):
     """Max over ranks of a host float: every rank's timed region ends when the
     slowest does (NCCL reduces a device tensor, gloo a host one)."""
@@ -213,12 +255,14 @@ def train_stops(torch, svf, ix, Qtr, gt_cal, ncal, precisions):
 
 # ---------------------------------------------------------------- serving
 def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zipf_s=1.1, max_inflight=8,
-                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048, window=None):
+                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048, window=None, small=None):
     """Open-loop Poisson stream at `rate` requests/s for `duration` s through
     the continuous-batching server: 90:9:1 search:insert:delete requests,
     batch sizes floor(exp(U[0, ln max_batch])), query components ~ Zipf(s).
-    Returns latency percentiles (ms) per op over the requests that arrived
-    after `warm` s, query and insert throughput, and cache counters."""
+    small = (b, cfg_small): search batches of at most b queries run with
+    cfg_small (several warps per query).  Returns latency percentiles (ms)
+    per op over the requests that arrived after `warm` s, query and insert
+    throughput, and cache counters."""
     rng = np.random.default_rng(seed)
     m = synth.MIXTURES[mix]
     arr, ops, sizes = [], [], []
@@ -256,7 +300,8 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     t0 = svf.Server.now() + 0.5
     for tag, (ta, op, sz) in enumerate(zip(arr, ops, sizes)):
         if op == 0:
-            srv.search(tag, Qall[qo:qo + sz], cfg, ids_out[qo:qo + sz], d_out[qo:qo + sz], t_arrival=t0 + ta)
+            c = small[1] if small and sz <= small[0] else cfg
+            srv.search(tag, Qall[qo:qo + sz], c, ids_out[qo:qo + sz], d_out[qo:qo + sz], t_arrival=t0 + ta)
             qo += sz
         elif op == 1:
             sz = min(sz, X_ins.shape[0] - io, ix.n_cap - n_used)
@@ -274,12 +319,15 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     srv.stop()
     st = ix.stats()
     lat = {0: [], 1: [], 2: []}
+    by_size = {"le16": [], "gt16": []}  # search latency by batch size
     done_q = done_i = 0
     t_first, t_last = None, None
     for c in comps:
         if c["t_arrival"] - t0 < warm:
             continue
         lat[c["op"]].append(1e3 * (c["t_done"] - c["t_arrival"]))
+        if c["op"] == 0:
+            by_size["le16" if c["count"] <= 16 else "gt16"].append(lat[0][-1])
         if c["op"] == 0:
             done_q += c["count"]
         elif c["op"] == 1:
@@ -294,6 +342,8 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     out = {"rate_req_per_s": rate, "duration_s": duration, "warmup_s": warm, "requests": len(comps),
            "qps": done_q / span, "inserts_per_s": done_i / span,
            "latency_ms": {names[o]: {"p50": pct(v, 50), "p99": pct(v, 99), "n": len(v)} for o, v in lat.items()},
+           "search_latency_ms_by_batch": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "n": len(v)}
+                                          for k, v in by_size.items()},
            "cache_hit_rate": (st["cache_hits"] / max(1, st["cache_hits"] + st["cache_misses"]))
            if st["cache_hits"] + st["cache_misses"] else None,
            "promoted": st["promoted"], "evicted": st["evicted"]}
@@ -416,18 +466,28 @@ def serve_main(a, svf, torch, log_t):
             op = (cfg, r)
             break
     cfg, rec = op if op else (cfg, r)
+    # batches of up to --serve-small queries: 8 warps per query (measured before tiering)
+    sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target, Ws=(1, 8)) if a.serve_small > 0 else {}
+    log_t("small batches", {W: {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()})
+    small = (a.serve_small, sb[8]["cfg"]) if 8 in sb else None
     slots = int(8e9 // (128 * 4))
     ix.enable_tier(M=slots, theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
     ix.release_device_store()
     del X
     log_t("tiered", slots)
     X_ins = synth.sample_chunked("serve128", 1_500_000, 503)
-    res = []
+    res, res1 = [], []
     for i, rate in enumerate(float(x) for x in a.serve_rates.split(",")):
         r = serve_stream(svf, torch, ix, "serve128", X_ins[i * 300_000:(i + 1) * 300_000], rate, a.serve_seconds,
-                         2.0, 510 + i, cfg)
+                         2.0, 510 + i, cfg, small=small)
         res.append(r)
         log_t("rate", rate, json.dumps(r))
+        if small and a.serve_compare:
+            # the same stream with one warp per query throughout
+            r = serve_stream(svf, torch, ix, "serve128", X_ins[i * 300_000:(i + 1) * 300_000], rate,
+                             a.serve_seconds, 2.0, 510 + i, cfg)
+            res1.append(r)
+            log_t("rate one warp", rate, json.dumps(r))
     p99 = [x["latency_ms"]["search"]["p99"] for x in res if x["latency_ms"]["search"]["p99"] is not None]
     out = {"metric": "serving p99 search latency (ms) at offered load", "value": min(p99) if p99 else None,
            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
@@ -435,8 +495,13 @@ def serve_main(a, svf, torch, log_t):
                       "build": f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins={a.serve_lins}, T_ins={a.serve_tins})",
                       "cache_rows": slots, "L": cfg.L,
                       "T": cfg.T, "recall@10": rec, "mix": "90:9:1", "batch": "log-uniform 1..2048",
-                      "queries": "Zipf(1.1) over components"},
+                      "queries": "Zipf(1.1) over components",
+                      "small_batches": (f"batches of <= {small[0]} queries: W = 8, T = {small[1].T}" if small
+                                        else None)},
+           "small_batch": {str(W): {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()},
            "rates": res}
+    if res1:
+        out["rates_one_warp"] = res1
     print(json.dumps(out), flush=True)
     return 0
 
@@ -468,7 +533,9 @@ def main():
     Qe_np = synth.sample_chunked("unit96", a.nq, 302 + rank)
     log_t("data", X.shape)
     policies = [p for p in a.serve_policies.split(",") if p]
-    ix = build_index(svf, torch, X, log_t, streams=1 + len(policies))
+    # capacity for the inserts of every serving stream: the main one, the
+    # one-warp-per-query rerun and the placement ablation
+    ix = build_index(svf, torch, X, log_t, streams=2 + len(policies))
     Xd = ix.vectors()[:a.n]
     Qe = torch.from_numpy(Qe_np).cuda()
     gt = exact_knn(svf, Xd, Qe, K, "ip")
@@ -588,6 +655,9 @@ def main():
     e1.synchronize()
     e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
     clk = clocks.stop(torch.cuda.current_device())
+    # ---- latency-bound batches: several warps per query (not timed above)
+    sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target)
+    log_t("small batches", {W: {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()})
 
     # ---- roofline of the search kernel (the only launch of a step)
     nq = a.nq
@@ -622,6 +692,10 @@ def main():
                 "h2d_bytes_per_step": Qh.numel() * 4, "d2h_bytes_per_step": ids_h.numel() * 4 + d_h.numel() * 4},
         "gpu_launches": a.steps,
         "clocks": clk,
+        "small_batch": {"form": form, "L": cfg.L,
+                        "note": "W warps per query expand W parents per iteration; latency of one call of the "
+                                "public API on a batch of b queries (CUDA events, host overhead included)",
+                        "by_W": {str(W): {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()}},
     }
     # serving: the same index with its fp32 rows tiered behind a device cache
     # of 31 % of them (the 8 GB : 25.6 GB ratio of the 50M serving workload),
@@ -641,6 +715,9 @@ def main():
             trav = "fp32 traversal through the tier"
         else:
             trav = "fp8 traversal + exact re-rank"
+        # batches of up to 16 queries take the several-warps-per-query path
+        if a.serve_trav != "fp32" and 8 in sb:
+            sopt["small"] = (16, sb[8]["cfg"])
         out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg,
                                       **sopt)
         qmix = (f"queries from a window of {win_arg[0]} components moving {win_arg[1]:g}/s" if win_arg
@@ -649,7 +726,16 @@ def main():
                                       f"{tier['M'] / 1e6:.1f}M-row device cache, {trav}, {qmix}, 90:9:1 mix, "
                                       "batches log-uniform 1..2048")
         out["serving"]["policy"] = "wavp"
+        if "small" in sopt:
+            out["serving"]["small_batches"] = f"batches of <= 16 queries: W = 8, T = {sb[8]['T']}"
         log_t("serving", json.dumps(out["serving"]))
+        if "small" in sopt:
+            # the same stream (same seed, re-tiered cache) with one warp per query throughout
+            ix.reset_tier(policy="wavp", **tier)
+            one = dict(sopt, small=None)
+            out["serving_one_warp"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds,
+                                                   1.0, 306, cfg, **one)
+            log_t("serving one warp per query", json.dumps(out["serving_one_warp"]))
         # placement ablation: the same stream (same seed) after re-tiering the
         # same index under each other policy
         if policies:

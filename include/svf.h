@@ -120,7 +120,15 @@ typedef struct {
  *   hash_log2 per-query visited-table size, log2 of slots (0: automatic)
  *   trace_feat  device [nq][T][16] float, or NULL: per-iteration features
  *   trace_meta  device [nq][2] int32 (iterations run, last top-k change)
- *   pool_out  device [nq][L] uint64 keys of the final pool, or NULL */
+ *   pool_out  device [nq][L] uint64 keys of the final pool, or NULL
+ *   W         parents per iteration, 0/1, 2, 4 or 8 (intra-query parallelism,
+ *             Sec. 4.4): with W > 1 each query runs on a CTA of W warps and
+ *             every iteration expands the W nearest unexpanded pool entries
+ *             (an id named by two parents is visited once); T counts
+ *             iterations, so a query expands up to W*T parents.  W > 1 does
+ *             not combine with mlp / trace_feat / trace_meta (SVF_EINVAL).
+ *             Meant for small batches, where one warp per query leaves most
+ *             of the GPU idle. */
 typedef struct {
     int32_t k;
     int32_t L;
@@ -137,7 +145,7 @@ typedef struct {
     int32_t *trace_meta;
     uint64_t *pool_out;
     int32_t t_every;
-    int32_t reserved0;
+    int32_t W;
 } svf_search_params;
 
 /* Running counters (since svf_create or svf_stats_reset). */

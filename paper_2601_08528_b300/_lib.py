@@ -50,7 +50,7 @@ class SearchParams(C.Structure):
                 ("rerank", C.c_int32), ("t_min", C.c_int32), ("mlp", C.c_void_p), ("z_tau", C.c_float),
                 ("hash_log2", C.c_int32), ("qkeys", C.c_void_p), ("seed", C.c_uint64), ("trace_feat", C.c_void_p),
                 ("trace_meta", C.c_void_p), ("pool_out", C.c_void_p), ("t_every", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("W", C.c_int32)]
 
 
 class Counters(C.Structure):

@@ -197,12 +197,15 @@ int svf_build(svf_index *h, const void *X, int64_t n, void *stream) {
     return SVF_OK;
 }
 
-static int hash_bits_for(int L, int R, int req) {
+// Visited-table size (log2 slots) for a pool of L and up to R new ids per
+// iteration: never more than half full before a reset; by default the
+// smallest power of two >= 4 (L + span * R), and at least 2^10.
+static int hash_bits_for(int L, int R, int req, int span = 1) {
     int need = 1;
     while ((1 << need) < 2 * (L + R)) need++;  // table at most half full
     if (req) return req < need ? need : req;
     int b = 1;
-    while ((1 << b) < 4 * (L + R)) b++;
+    while ((1 << b) < 4 * (L + span * R)) b++;
     return b < 10 ? 10 : b;
 }
 
@@ -222,7 +225,11 @@ static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search
     a.seed = sp->seed ? sp->seed : h->p.seed;
     a.k = sp->k;
     a.T = sp->T;
-    a.hash_bits = hash_bits_for(sp->L, h->p.R, sp->hash_log2);
+    a.W = sp->W > 1 ? sp->W : 1;
+    // up to W*R new ids per iteration (W parents); with W > 1 the default
+    // table holds about four iterations' ids, so resets stay as rare as with
+    // one parent per iteration
+    a.hash_bits = hash_bits_for(sp->L, a.W * h->p.R, sp->hash_log2, a.W > 1 ? 4 : 1);
     a.rerank = sp->rerank;
     a.out_dtype = h->p.dtype;
     a.out_ids = out_ids;
@@ -260,6 +267,10 @@ int svf_search(svf_index *h, const void *Q, int64_t nq, const svf_search_params 
     }
     if (sp->rerank && trav.dtype == h->p.dtype) return fail(SVF_EINVAL, "re-rank applies to low-precision traversal");
     if (sp->mlp && sp->t_min < 1) return fail(SVF_EINVAL, "t_min must be >= 1 with a stop network");
+    if (sp->W != 0 && sp->W != 1 && sp->W != 2 && sp->W != 4 && sp->W != 8)
+        return fail(SVF_EINVAL, "W must be 0, 1, 2, 4 or 8");
+    if (sp->W > 1 && (sp->mlp || sp->trace_feat || sp->trace_meta))
+        return fail(SVF_EINVAL, "the stop network and traces run with one warp per query (W <= 1)");
     h->last = (cudaStream_t)stream;
     return search_impl(h, Q, nq, sp, out_ids, out_dist, (cudaStream_t)stream, h->n_used, trav);
 }

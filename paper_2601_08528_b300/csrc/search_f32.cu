@@ -1,10 +1,14 @@
 // search_f32.cu -- instantiations of the search kernel for FP32 traversal.
-#include "search_kernel.cuh"
+#include "search_multi.cuh"
 
 namespace svf {
 
 cudaError_t launch_search_f32(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st) {
     return launch_search_dtype<SVF_F32, 32>(a, R, LW, learn, smem, st);
+}
+
+cudaError_t launch_multi_f32(const SearchArgs &a, int R, int W, int LW, size_t smem, cudaStream_t st) {
+    return launch_multi_dtype<SVF_F32, 32>(a, R, W, LW, smem, st);
 }
 
 }  // namespace svf

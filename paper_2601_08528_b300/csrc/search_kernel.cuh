@@ -92,6 +92,63 @@ __device__ __forceinline__ float pool_dist(const uint64_t (&pool)[LW], int e, in
     return dtype == SVF_U8 ? (float)(int32_t)v : __uint_as_float(v);
 }
 
+// The top k (k <= 32: slot 0) and, if asked for, the whole final pool.
+template <int LW>
+__device__ __forceinline__ void write_out(const SearchArgs &a, const uint64_t (&pool)[LW], int lane, int64_t qi) {
+    constexpr int L = 32 * LW;
+    if (lane < a.k) {
+        uint64_t k0 = pool[0];
+        bool pad = key_is_pad(k0);
+        a.out_ids[qi * a.k + lane] = pad ? kEmpty : key_id(k0);
+        a.out_dist[qi * a.k + lane] = key_to_out(pad ? 0xFFFFFFFFu : (uint32_t)(k0 >> 32), a.out_dtype, a.trav.metric);
+    }
+    if (a.pool_out) {
+#pragma unroll
+        for (int s = 0; s < LW; s++) {
+            uint64_t k0 = pool[s];
+            a.pool_out[qi * L + s * 32 + lane] =
+                key_is_pad(k0) ? kPad : (k0 & ~(uint64_t)(kExpBit | kNewBit));
+        }
+    }
+}
+
+// The end of a query, warp-wide: the optional exact re-rank of the final
+// pool from the primary store, the top k out and the pool out.  False if a
+// row copy gave up (SVF_ETIMEOUT recorded).
+template <int LW>
+__device__ __forceinline__ bool finish_pool(const SearchArgs &a, uint64_t (&pool)[LW], uint32_t *list, uint64_t *keys,
+                                            Stage &stg, const float *qf, const uint8_t *qb, int lane, int64_t qi,
+                                            int &hits, int &misses) {
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    // ---- optional exact re-rank of the final pool from the primary store
+    if (a.rerank) {
+        int npool = 0;
+#pragma unroll
+        for (int s = 0; s < LW; s++) {
+            bool real = !key_is_pad(pool[s]);
+            uint32_t b = __ballot_sync(kFull, real);
+            if (real) list[npool + __popc(b & lt_mask)] = key_id(pool[s]);
+            npool += __popc(b);
+        }
+        __syncwarp();
+        // the fp32 query is still in shared memory
+        if (!staged_dist<SVF_F32>(stg, a.prim, list, npool, keys, 0u, lane, qf, qb, a.prim.map ? &a.tier : nullptr,
+                                  &hits, &misses)) {
+            if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
+            return false;
+        }
+#pragma unroll
+        for (int s = 0; s < LW; s++) {
+            int e = s * 32 + lane;
+            pool[s] = e < npool ? keys[e] : kPad;
+        }
+        warp_sort<LW>(pool, lane);
+    }
+
+    write_out<LW>(a, pool, lane, qi);
+    return true;
+}
+
 // NCH > 0: the traversal rows are NCH 16-byte chunks (the launcher checks
 // the store against it); 0: any layout, read from a.trav at run time.
 template <int DT, int R, int LW, bool LEARN, int NCH>
@@ -403,46 +460,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         }
     }
 
-    // ---- optional exact re-rank of the final pool from the primary store
-    if (a.rerank) {
-        int npool = 0;
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            bool real = !key_is_pad(pool[s]);
-            uint32_t b = __ballot_sync(kFull, real);
-            if (real) list[npool + __popc(b & lt_mask)] = key_id(pool[s]);
-            npool += __popc(b);
-        }
-        __syncwarp();
-        // the fp32 query is still in shared memory
-        if (!staged_dist<SVF_F32>(stg, a.prim, list, npool, keys, 0u, lane, qf, qb, a.prim.map ? &a.tier : nullptr,
-                                  &hits, &misses)) {
-            if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
-            return;
-        }
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            int e = s * 32 + lane;
-            pool[s] = e < npool ? keys[e] : kPad;
-        }
-        warp_sort<LW>(pool, lane);
-    }
-
-    // ---- top-k out (k <= 32: slot 0)
-    if (lane < a.k) {
-        uint64_t k0 = pool[0];
-        bool pad = key_is_pad(k0);
-        a.out_ids[qi * a.k + lane] = pad ? kEmpty : key_id(k0);
-        a.out_dist[qi * a.k + lane] = key_to_out(pad ? 0xFFFFFFFFu : (uint32_t)(k0 >> 32), a.out_dtype, a.trav.metric);
-    }
-    if (a.pool_out) {
-#pragma unroll
-        for (int s = 0; s < LW; s++) {
-            uint64_t k0 = pool[s];
-            a.pool_out[qi * L + s * 32 + lane] =
-                key_is_pad(k0) ? kPad : (k0 & ~(uint64_t)(kExpBit | kNewBit));
-        }
-    }
+    if (!finish_pool<LW>(a, pool, list, keys, stg, qf, qb, lane, qi, hits, misses)) return;
     if (a.trace_meta && lane == 0) {
         a.trace_meta[qi * 2 + 0] = ran;
         a.trace_meta[qi * 2 + 1] = fs.t_last;
@@ -452,7 +470,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         atomicAdd(a.status + kStIters, (unsigned long long)iters);
         atomicAdd(a.status + kStEvals, (unsigned long long)evals);
         if (resets) atomicAdd(a.status + kStResets, (unsigned long long)resets);
-        if (tier) {
+        if (hits | misses) {  // traversal or re-rank rows read through a tiered store
             atomicAdd(a.status + kStHits, (unsigned long long)hits);
             atomicAdd(a.status + kStMisses, (unsigned long long)misses);
         }

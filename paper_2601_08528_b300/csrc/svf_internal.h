@@ -23,6 +23,20 @@ inline int sm_count() {
 
 constexpr int kSearchWarps = 4;  // queries (warps) per CTA
 
+// Several warps per query (search_multi.cuh): W parents per iteration.
+constexpr int kMultiMaxW = 8;
+struct MultiCtl {
+    uint32_t par[kMultiMaxW];  // this iteration's parents, nearest first
+    uint64_t worst;            // the pool's L-th key (flags masked) before the merge
+    int npar;
+    int nadm;                  // admitted keys appended this iteration
+    int nf;                    // ids staged this iteration (fresh, deletions included)
+    int nlive;                 // of them, not deleted
+    int nrows;                 // rows of a list scored by all warps (initial pool, re-rank)
+    int abort;                 // a row copy gave up: every warp leaves
+};
+constexpr size_t kMultiCtlBytes = (sizeof(MultiCtl) + 15) / 16 * 16;
+
 struct SearchArgs {
     RowDesc trav;  // store read by the traversal
     RowDesc prim;  // primary store (exact re-rank)
@@ -53,6 +67,7 @@ struct SearchArgs {
     int list_len;
     uint32_t stage_bytes;
     size_t warp_smem;
+    int W;            // warps (parents per iteration) per query; 1: one warp per query
 };
 
 cudaError_t launch_search(SearchArgs a, int R, int L, cudaStream_t st);

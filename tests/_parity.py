@@ -69,3 +69,21 @@ def recall(ids, true_ids, true_d, found_d_exact):
     kth = true_d[:, k - 1:k]
     ok = (as_u32(ids) != 0xFFFFFFFF) & (found_d_exact <= kth * (1 + 1e-12) + 1e-300)
     return float(ok.sum()) / (ids.shape[0] * k)
+
+
+def rerank_ref(orc, st, Q, o, k):
+    """Oracle of the exact re-rank: FP64 distances (store `st`) of the final
+    low-precision-traversal pool o["pool_ids"], re-sorted by (dist, id); the
+    gap also covers the re-sorted k-boundary."""
+    pd = orc.dist_ids(st, Q, o["pool_ids"])
+    nq = len(Q)
+    want_i = np.empty((nq, k), np.int64)
+    want_d = np.empty((nq, k))
+    gaps = np.empty(nq)
+    for q in range(nq):
+        order = np.lexsort((o["pool_ids"][q], pd[q]))
+        want_i[q] = o["pool_ids"][q][order[:k]]
+        want_d[q] = pd[q][order[:k]]
+        s = pd[q][order[:k + 1]]
+        gaps[q] = np.min(np.abs(np.diff(s))) if len(s) > 1 else np.inf
+    return {"ids": want_i, "dist": want_d, "gap": np.minimum(gaps, o["gap"])}

@@ -64,17 +64,7 @@ def test_rerank_is_exact_fp32_over_the_final_pool(svf, orc, prec):
                           svf.SearchConfig(k=10, L=L, T=32, precision=prec, rerank=True, seed=4))
     o = orc.search(lst, 3000, g, None, Q, 10, L, 32, 4, want_pool=True)
     # oracle: exact FP64 distances of the whole final pool, re-sorted by (dist, id)
-    pd = orc.dist_ids(st, Q, o["pool_ids"])
-    want_i = np.empty((len(Q), 10), np.int64)
-    want_d = np.empty((len(Q), 10))
-    gaps = np.empty(len(Q))
-    for q in range(len(Q)):
-        order = np.lexsort((o["pool_ids"][q], pd[q]))
-        want_i[q] = o["pool_ids"][q][order[:10]]
-        want_d[q] = pd[q][order[:10]]
-        s = pd[q][order[:11]]
-        gaps[q] = np.min(np.abs(np.diff(s))) if len(s) > 1 else np.inf
-    ref = {"ids": want_i, "dist": want_d, "gap": np.minimum(gaps, o["gap"])}
+    ref = P.rerank_ref(orc, st, Q, o, 10)
     P.check_fp32(ids.cpu().numpy(), dist.cpu().numpy(), ref, X, Q, "ip")
 
 

@@ -89,17 +89,7 @@ def test_unit96_10M_lowp_rerank_search_sampled(svf, orc, unit96, prec):
     o = orc.search(lst, N96, g, None, Q[qs], 10, L96, T96, SEED, want_pool=True)
     # oracle: exact FP64 distances of the final low-precision-traversal pool, re-sorted by (dist, id)
     st = orc.Store.from_vectors(X, "ip")
-    pd = orc.dist_ids(st, Q[qs], o["pool_ids"])
-    want_i = np.empty((len(qs), 10), np.int64)
-    want_d = np.empty((len(qs), 10))
-    gaps = np.empty(len(qs))
-    for q in range(len(qs)):
-        order = np.lexsort((o["pool_ids"][q], pd[q]))
-        want_i[q] = o["pool_ids"][q][order[:10]]
-        want_d[q] = pd[q][order[:10]]
-        s = pd[q][order[:11]]
-        gaps[q] = np.min(np.abs(np.diff(s))) if len(s) > 1 else np.inf
-    ref = {"ids": want_i, "dist": want_d, "gap": np.minimum(gaps, o["gap"])}
+    ref = P.rerank_ref(orc, st, Q[qs], o, 10)
     P.check_fp32(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], ref, X, Q[qs], "ip")
 
 
