@@ -67,6 +67,8 @@ def lib():
             "orc_search": (I32, [S, I64, P, I32, P, P, I64, P, I32, I32, I32, U64, I32, P, P, P, P, P, P, P]),
             "orc_insert": (None, [S, I64, I64, P, I32, P, I32, I32, U64, I32, P, P]),
             "orc_delete": (I64, [S, I64, P, I32, P, P, I64, I32, I32, P, P]),
+            "orc_consolidate": (I64, [S, I64, P, I32, P, I32, I32, P]),
+            "orc_reverse_patch": (None, [S, P, I32, P, I64, I64, P, I64, P]),
             "orc_threads": (I32, []),
             "orc_set_threads": (None, [I32]),
             "orc_mlp_forward": (None, [P, P, P, D, P, I64, P, P]),
@@ -269,6 +271,33 @@ def delete(store: Store, n_used: int, graph: np.ndarray, delbits: np.ndarray, id
     newly = lib().orc_delete(C.byref(st), n_used, _p(graph), R, _p(delbits), _p(ids), len(ids), c, mode,
                              _p(rep), _p(gap))
     return int(newly), int(rep[0]), gap[:n_used]
+
+
+def consolidate(store: Store, n0: int, graph: np.ndarray, delbits: np.ndarray, cap: int = 512,
+                mode: int = PRUNE_RNG):
+    """Global consolidation of graph rows [0, n0) (in place) under the
+    deletion bits `delbits`.  Returns (rewritten_rows, rows_gap [n0])."""
+    assert graph.flags.c_contiguous and graph.dtype == np.uint32
+    R = graph.shape[1]
+    gap = np.zeros(max(n0, 1), dtype=np.float64)
+    st = store.c()
+    nrep = lib().orc_consolidate(C.byref(st), n0, _p(graph), R, _p(delbits), cap, mode, _p(gap))
+    if nrep < 0:
+        raise ValueError("cap must be >= R")
+    return int(nrep), gap[:n0]
+
+
+def reverse_patch(store: Store, graph: np.ndarray, delbits: np.ndarray | None, n0: int, rows: np.ndarray, tmax: int):
+    """The reverse edges of new vertices n0 .. n0+m-1 (graph rows `rows`)
+    applied to the tails of their targets < tmax (in place).  Returns the
+    per-target gap [tmax]."""
+    assert graph.flags.c_contiguous and graph.dtype == np.uint32
+    rows = np.ascontiguousarray(rows, dtype=np.uint32)
+    R = graph.shape[1]
+    gap = np.zeros(max(tmax, 1), dtype=np.float64)
+    st = store.c()
+    lib().orc_reverse_patch(C.byref(st), _p(graph), R, _p(delbits), n0, rows.shape[0], _p(rows), tmax, _p(gap))
+    return gap[:tmax]
 
 
 def recall_at_k(found: np.ndarray, true_ids: np.ndarray, true_d: np.ndarray, found_d_exact: np.ndarray) -> float:

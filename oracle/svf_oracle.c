@@ -819,57 +819,23 @@ static int rev_cmp(const void *pa, const void *pb) {
     return (a->src > b->src) - (a->src < b->src);
 }
 
-void orc_insert(const orc_store *X, int64_t n0, int64_t m, uint32_t *graph, int32_t R, const uint32_t *del,
-                int32_t L_ins, int32_t T_ins, uint64_t seed, int32_t mode, double *new_gap, double *tail_gap) {
+/* Reverse edges of new vertices n0 .. n0+m-1 whose rows are rows[m][R], with
+   rowd / rows_s the distances (and scales) of those entries: every named
+   target u < tmax keeps as its tail half [R/2, R) the R/2 best (dist, id) of
+   its live tail entries (ids < n0) and the new vertices that chose it; the
+   head half is kept.  tail_gap (optional): per target, the smallest decisive
+   gap of its merge (INFINITY for untouched u < tmax). */
+static void reverse_patch(const orc_store *X, uint32_t *graph, int32_t R, const uint32_t *del, int64_t n0,
+                          int64_t m, const uint32_t *rows, const double *rowd, const double *rows_s, int64_t tmax,
+                          double *tail_gap) {
     int d = X->d;
-    srch_ctx S = {n0, graph, R, del, L_ins, T_ins, L_ins, seed};
-    uint32_t *rows = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1) * R);
-    double *rowd = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * R);
-    double *rows_s = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * R);
-#pragma omp parallel
-    {
-        double *q = (double *)malloc(sizeof(double) * d);
-        double *x = (double *)malloc(sizeof(double) * d);
-        double *xb = (double *)malloc(sizeof(double) * d);
-        ent *pool = (ent *)malloc(sizeof(ent) * (L_ins + R + 1));
-        ent *buf = (ent *)malloc(sizeof(ent) * (L_ins + R + 1));
-#pragma omp for schedule(dynamic, 1)
-        for (int64_t i = 0; i < m; i++) {
-            int64_t v = n0 + i;
-            const uint8_t *raw = (const uint8_t *)X->data + v * X->pitch;
-            uint64_t key = orc_query_key(raw, query_bytes(X));
-            decode_row(X, v, q);
-            int np;
-            srch_stat st;
-            double g = search_one(X, &S, q, key, pool, &np, &st, x, buf, NULL);
-            uint32_t *out = rows + i * R;
-            double g2 = prune_core(X, pool, np, mode, graph, R, R, out, x, xb);
-            if (g2 < g) g = g2;
-            for (int r = 0; r < R; r++) {
-                rowd[i * R + r] = INFINITY;
-                rows_s[i * R + r] = 0.0;
-                for (int j = 0; j < np; j++)
-                    if (pool[j].id == out[r]) {
-                        rowd[i * R + r] = pool[j].d;
-                        rows_s[i * R + r] = pool[j].s;
-                        break;
-                    }
-            }
-            if (new_gap) new_gap[i] = g;
-        }
-        free(q);
-        free(x);
-        free(xb);
-        free(pool);
-        free(buf);
-    }
     /* reverse-edge requests (u, v, dist(u, v)) */
     int64_t nreq = 0;
     revreq *req = (revreq *)malloc(sizeof(revreq) * (size_t)(m > 0 ? m : 1) * R);
     for (int64_t i = 0; i < m; i++)
         for (int r = 0; r < R; r++) {
             uint32_t u = rows[i * R + r];
-            if (u == ORC_EMPTY) continue;
+            if (u == ORC_EMPTY || (int64_t)u >= tmax) continue;
             req[nreq].target = u;
             req[nreq].src = (uint32_t)(n0 + i);
             req[nreq].d = rowd[i * R + r];
@@ -878,7 +844,7 @@ void orc_insert(const orc_store *X, int64_t n0, int64_t m, uint32_t *graph, int3
         }
     qsort(req, (size_t)nreq, sizeof(revreq), rev_cmp);
     if (tail_gap)
-        for (int64_t u = 0; u < n0; u++) tail_gap[u] = INFINITY;
+        for (int64_t u = 0; u < tmax; u++) tail_gap[u] = INFINITY;
     int H = R / 2, TL = R - R / 2;
     /* group starts */
     int64_t ngrp = 0;
@@ -926,45 +892,76 @@ void orc_insert(const orc_store *X, int64_t n0, int64_t m, uint32_t *graph, int3
         free(xb);
         free(mg);
     }
-    for (int64_t i = 0; i < m; i++) memcpy(graph + (n0 + i) * R, rows + i * R, sizeof(uint32_t) * R);
     free(gs);
     free(req);
+}
+
+void orc_insert(const orc_store *X, int64_t n0, int64_t m, uint32_t *graph, int32_t R, const uint32_t *del,
+                int32_t L_ins, int32_t T_ins, uint64_t seed, int32_t mode, double *new_gap, double *tail_gap) {
+    int d = X->d;
+    srch_ctx S = {n0, graph, R, del, L_ins, T_ins, L_ins, seed};
+    uint32_t *rows = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1) * R);
+    double *rowd = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * R);
+    double *rows_s = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * R);
+#pragma omp parallel
+    {
+        double *q = (double *)malloc(sizeof(double) * d);
+        double *x = (double *)malloc(sizeof(double) * d);
+        double *xb = (double *)malloc(sizeof(double) * d);
+        ent *pool = (ent *)malloc(sizeof(ent) * (L_ins + R + 1));
+        ent *buf = (ent *)malloc(sizeof(ent) * (L_ins + R + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < m; i++) {
+            int64_t v = n0 + i;
+            const uint8_t *raw = (const uint8_t *)X->data + v * X->pitch;
+            uint64_t key = orc_query_key(raw, query_bytes(X));
+            decode_row(X, v, q);
+            int np;
+            srch_stat st;
+            double g = search_one(X, &S, q, key, pool, &np, &st, x, buf, NULL);
+            uint32_t *out = rows + i * R;
+            double g2 = prune_core(X, pool, np, mode, graph, R, R, out, x, xb);
+            if (g2 < g) g = g2;
+            for (int r = 0; r < R; r++) {
+                rowd[i * R + r] = INFINITY;
+                rows_s[i * R + r] = 0.0;
+                for (int j = 0; j < np; j++)
+                    if (pool[j].id == out[r]) {
+                        rowd[i * R + r] = pool[j].d;
+                        rows_s[i * R + r] = pool[j].s;
+                        break;
+                    }
+            }
+            if (new_gap) new_gap[i] = g;
+        }
+        free(q);
+        free(x);
+        free(xb);
+        free(pool);
+        free(buf);
+    }
+    reverse_patch(X, graph, R, del, n0, m, rows, rowd, rows_s, n0, tail_gap);
+    for (int64_t i = 0; i < m; i++) memcpy(graph + (n0 + i) * R, rows + i * R, sizeof(uint32_t) * R);
     free(rows);
     free(rowd);
     free(rows_s);
 }
 
-/* ------------------------------------------------------------------ */
-/* Delete (Sec. 5.2).  Returns the number of newly deleted ids, or -1 when
-   some id >= n_used (nothing is changed then).  After marking, every live
-   vertex u with more than half (strictly, 2*#deleted > R) of its row deleted
-   is repaired from a snapshot of the graph:
-     candidates = u's live row entries in row order, then for each deleted
-     p in u's row (row order) the first c entries of N_out(p) that are live,
-     not u and not yet candidates; sorted by (dist(u, .), id); reordered by
-     orc_prune; if fewer than R survive, u's deleted entries fill the
-     remaining slots in their original order (then EMPTY).
-   out_repaired (optional): number of repaired rows.  rows_gap[n_used]
-   (optional): smallest decisive gap of each repaired row (INFINITY
-   elsewhere). */
-int64_t orc_delete(const orc_store *X, int64_t n_used, uint32_t *graph, int32_t R, uint32_t *del,
-                   const uint32_t *ids, int64_t m, int32_t c, int32_t mode, int64_t *out_repaired,
-                   double *rows_gap) {
-    for (int64_t i = 0; i < m; i++)
-        if ((int64_t)ids[i] >= n_used) return -1;
-    int64_t newly = 0;
-    for (int64_t i = 0; i < m; i++)
-        if (!is_deleted(del, ids[i])) {
-            del[ids[i] >> 5] |= 1u << (ids[i] & 31);
-            newly++;
-        }
+/* Repair (Sec. 5.2) of every live vertex u < n_used whose snapshot row has
+   at least min_del deleted entries: candidates = u's live row entries in row
+   order, then for each deleted p in u's row (row order) the first c entries
+   of N_out(p) that are live, not u and not yet candidates, at most cap in
+   all; sorted by (dist(u, .), id); reordered by prune_core (N_out from the
+   snapshot); if fewer than R survive, u's deleted entries fill the remaining
+   slots in their original order (then EMPTY).  Reads only snap, writes the
+   new rows into graph.  Returns the number of rewritten rows. */
+static int64_t repair_rows(const orc_store *X, int64_t n_used, uint32_t *graph, const uint32_t *snap, int32_t R,
+                           const uint32_t *del, int32_t c, int32_t min_del, int32_t cap, int32_t mode,
+                           double *rows_gap) {
     int d = X->d;
-    uint32_t *snap = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_used > 0 ? n_used : 1) * R);
-    memcpy(snap, graph, sizeof(uint32_t) * (size_t)n_used * R);
     int64_t nrep = 0;
     if (rows_gap)
         for (int64_t u = 0; u < n_used; u++) rows_gap[u] = INFINITY;
-    int cap = R + c * R;
 #pragma omp parallel reduction(+ : nrep)
     {
         double *xa = (double *)malloc(sizeof(double) * d);
@@ -978,7 +975,7 @@ int64_t orc_delete(const orc_store *X, int64_t n_used, uint32_t *graph, int32_t 
             int nd = 0;
             for (int r = 0; r < R; r++)
                 if (row[r] != ORC_EMPTY && is_deleted(del, row[r])) nd++;
-            if (2 * nd <= R) continue;
+            if (nd < min_del) continue;
             int nc = 0;
             for (int r = 0; r < R; r++) {
                 uint32_t t = row[r];
@@ -992,7 +989,7 @@ int64_t orc_delete(const orc_store *X, int64_t n_used, uint32_t *graph, int32_t 
                 if (p == ORC_EMPTY || !is_deleted(del, p)) continue;
                 const uint32_t *prow = snap + (int64_t)p * R;
                 int taken = 0;
-                for (int s = 0; s < R && taken < c; s++) {
+                for (int s = 0; s < R && taken < c && nc < cap; s++) {
                     uint32_t w = prow[s];
                     if (w == ORC_EMPTY || is_deleted(del, w) || w == (uint32_t)u) continue;
                     int dup = 0;
@@ -1029,9 +1026,91 @@ int64_t orc_delete(const orc_store *X, int64_t n_used, uint32_t *graph, int32_t 
         free(cd);
         free(out);
     }
+    return nrep;
+}
+
+
+/* ------------------------------------------------------------------ */
+/* Delete (Sec. 5.2).  Returns the number of newly deleted ids, or -1 when
+   some id >= n_used (nothing is changed then).  After marking, every live
+   vertex u with more than half (strictly, 2*#deleted > R) of its row deleted
+   is repaired from a snapshot of the graph:
+     candidates = u's live row entries in row order, then for each deleted
+     p in u's row (row order) the first c entries of N_out(p) that are live,
+     not u and not yet candidates; sorted by (dist(u, .), id); reordered by
+     orc_prune; if fewer than R survive, u's deleted entries fill the
+     remaining slots in their original order (then EMPTY).
+   out_repaired (optional): number of repaired rows.  rows_gap[n_used]
+   (optional): smallest decisive gap of each repaired row (INFINITY
+   elsewhere). */
+int64_t orc_delete(const orc_store *X, int64_t n_used, uint32_t *graph, int32_t R, uint32_t *del,
+                   const uint32_t *ids, int64_t m, int32_t c, int32_t mode, int64_t *out_repaired,
+                   double *rows_gap) {
+    for (int64_t i = 0; i < m; i++)
+        if ((int64_t)ids[i] >= n_used) return -1;
+    int64_t newly = 0;
+    for (int64_t i = 0; i < m; i++)
+        if (!is_deleted(del, ids[i])) {
+            del[ids[i] >> 5] |= 1u << (ids[i] & 31);
+            newly++;
+        }
+    uint32_t *snap = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_used > 0 ? n_used : 1) * R);
+    memcpy(snap, graph, sizeof(uint32_t) * (size_t)n_used * R);
+    int64_t nrep = repair_rows(X, n_used, graph, snap, R, del, c, R / 2 + 1, R + c * R, mode, rows_gap);
     free(snap);
     if (out_repaired) *out_repaired = nrep;
     return newly;
+}
+
+/* Global consolidation (Sec. 5.2), on the snapshot of Sec. 5.3's
+   multi-version mechanism: graph holds rows [0, n0) and del the deletion
+   bits of the moment the snapshot was taken.  Every live vertex with at
+   least one deleted out-neighbour is repaired as in orc_delete, taking every
+   live entry of each deleted neighbour's row (c = R), at most cap candidates
+   in all (u's live entries first, then the deleted neighbours in row order,
+   each row in order; cap >= R).  Returns the number of rewritten rows, or -1
+   for cap < R. */
+int64_t orc_consolidate(const orc_store *X, int64_t n0, uint32_t *graph, int32_t R, const uint32_t *del, int32_t cap,
+                        int32_t mode, double *rows_gap) {
+    if (cap < R) return -1; /* u's own live entries always fit */
+    uint32_t *snap = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n0 > 0 ? n0 : 1) * R);
+    memcpy(snap, graph, sizeof(uint32_t) * (size_t)n0 * R);
+    int64_t nrep = repair_rows(X, n0, graph, snap, R, del, R, 1, cap, mode, rows_gap);
+    free(snap);
+    return nrep;
+}
+
+/* Reverse Edge Integration (Sec. 5.3): the logged reverse edges of one insert
+   batch (new vertices n0 .. n0+m-1 with graph rows rows[m][R]) applied to a
+   consolidated graph; distances are recomputed here; targets >= tmax (rows
+   that are not part of the consolidated snapshot) are skipped. */
+void orc_reverse_patch(const orc_store *X, uint32_t *graph, int32_t R, const uint32_t *del, int64_t n0, int64_t m,
+                       const uint32_t *rows, int64_t tmax, double *tail_gap) {
+    int d = X->d;
+    double *rowd = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * R);
+    double *rows_s = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * R);
+#pragma omp parallel
+    {
+        double *xa = (double *)malloc(sizeof(double) * d);
+        double *xb = (double *)malloc(sizeof(double) * d);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < m; i++) {
+            decode_row(X, n0 + i, xa);
+            for (int r = 0; r < R; r++) {
+                uint32_t u = rows[i * R + r];
+                rowd[i * R + r] = INFINITY;
+                rows_s[i * R + r] = 0.0;
+                if (u == ORC_EMPTY) continue;
+                decode_row(X, u, xb);
+                rowd[i * R + r] = vdist(xa, xb, d, X->metric, &rows_s[i * R + r]);
+            }
+        }
+        free(xa);
+        free(xb);
+    }
+    reverse_patch(X, graph, R, del, n0, m, rows, rowd, rows_s, tmax, tail_gap);
+    free(rowd);
+    free(rows_s);
 }
 
 /* ------------------------------------------------------------------ */

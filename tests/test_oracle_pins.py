@@ -340,6 +340,80 @@ def test_search_w_parents_counts_and_range(orc):
             orc.search(st, n, g, None, Q, 10, 64, 4, 5, W=W)
 
 
+# ---------------------------------------------------------------- global consolidation (Sec. 5.2, 5.3)
+def _consolidate_case(orc):
+    g = _golden("consolidate_hand.json")
+    pts = np.array(g["points"], dtype=np.float32)
+    st = orc.Store.from_vectors(np.pad(pts, ((0, 0), (0, 2))), "l2")
+    n0 = g["n0"]
+    bits = orc.bitset(len(pts), g["delete"])
+    return g, st, n0, bits
+
+
+def test_consolidate_hand_worked(orc):
+    g, st, n0, bits = _consolidate_case(orc)
+    graph = np.array(g["graph"], dtype=np.uint32)
+    nrep, _ = orc.consolidate(st, n0, graph, bits)
+    assert graph.tolist() == g["consolidated"] and nrep == g["rewritten"]
+    capped = np.array(g["graph"], dtype=np.uint32)
+    orc.consolidate(st, n0, capped, bits, cap=g["R"])
+    assert capped.tolist() == g["consolidated_cap3"]
+    with pytest.raises(ValueError):
+        orc.consolidate(st, n0, capped, bits, cap=g["R"] - 1)
+    # the localized repair leaves rows with at most R/2 deleted entries alone
+    loc = np.array(g["graph"], dtype=np.uint32)
+    newly, rep, _ = orc.delete(st, n0, loc, orc.bitset(len(g["points"])), g["delete"])
+    assert (newly, rep) == (1, 0) and loc.tolist() == g["graph"]
+
+
+def test_reverse_edge_replay_hand_worked(orc):
+    g, st, n0, bits = _consolidate_case(orc)
+    rows = np.array([g["new_row"]], dtype=np.uint32)
+    for tmax, want in ((n0, g["replayed"]), (1, g["replayed_tmax1"])):
+        graph = np.array(g["consolidated"], dtype=np.uint32)
+        orc.reverse_patch(st, graph, bits, n0, rows, tmax)
+        assert graph.tolist() == want
+
+
+def test_reverse_edge_replay_equals_the_insert_patch(orc):
+    # replaying an insert batch's rows onto the graph the insert started from
+    # gives the rows the insert itself wrote (the same requests, distances
+    # recomputed)
+    n0, m, R = 1500, 120, 16
+    X = synth.sample("u8", n0 + m, 91)
+    st = orc.Store.from_vectors(X, "l2")
+    g0, _ = orc.build_graph(orc.Store.from_vectors(X[:n0], "l2"), R)
+    g = np.full((n0 + m, R), orc.EMPTY, dtype=np.uint32)
+    g[:n0] = g0
+    orc.insert(st, n0, m, g, None, 32, 16, 9)
+    r = np.full((n0 + m, R), orc.EMPTY, dtype=np.uint32)
+    r[:n0] = g0
+    orc.reverse_patch(st, r, None, n0, g[n0:], n0)
+    np.testing.assert_array_equal(r[:n0], g[:n0])
+
+
+def test_consolidation_of_every_affected_row(orc):
+    # invariants on a larger graph: after 20 % deletes every live row that
+    # named a deleted vertex names none (when enough live candidates exist),
+    # rows without deleted entries are unchanged, deleted rows are untouched
+    n, R = 2000, 16
+    X = synth.sample("u8", n, 95)
+    st = orc.Store.from_vectors(X, "l2")
+    g, _ = orc.build_graph(st, R)
+    dele = np.random.default_rng(96).choice(n, n // 5, replace=False)
+    bits = orc.bitset(n, dele)
+    isdel = np.zeros(n, bool)
+    isdel[dele] = True
+    before = g.copy()
+    nrep, _ = orc.consolidate(st, n, g, bits, cap=R * R + R)
+    named = np.array([(~isdel[u]) and isdel[before[u]].any() for u in range(n)])
+    assert nrep == named.sum()
+    np.testing.assert_array_equal(g[~named], before[~named])
+    left = np.array([isdel[g[u][g[u] != orc.EMPTY]].any() for u in range(n)])
+    assert left[named].mean() < 0.01
+    assert (g != np.arange(n)[:, None]).all()
+
+
 # ---------------------------------------------------------------- insert (Sec. 5.1)
 def test_insert_invariants_and_read_after_write(orc):
     n0, m, R = 1500, 200, 16
