@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--serve-trav", default="fp8", choices=["fp8", "fp32"],
                     help="unit96-10M serving stream: the measured fp8 form (traversal resident, re-rank rows "
                          "through the tier), or plain fp32 (every traversal row through the tier)")
+    ap.add_argument("--consolidate", type=int, default=1,
+                    help="unit96-10M: delete 20%% of the index and consolidate it (before the serving stream, "
+                         "which then runs on the consolidated index); 0 skips")
     ap.add_argument("--serve-small", type=int, default=16,
                     help="serve128-50M: search batches of at most this many queries run with 8 warps per query "
                          "(0: one warp per query throughout)")
@@ -195,6 +198,75 @@ def small_batch(svf, torch, ix, Q, gt, cfg, target, Ws=(1, 2, 4, 8), sizes=(1, 1
         row["cfg"] = c
         out[W] = row
     return out
+
+
+def consolidation(svf, torch, ix, Q, cfg, frac=0.2, frac2=0.05, seed=307, probes=400):
+    """Global consolidation (Sec. 5.2 under the multi-version mechanism of
+    Sec. 5.3) on the device-resident index.  Deletes `frac` of it (with the
+    localized repair), reports recall@10 of `cfg` against exact kNN over the
+    live vectors before and after a consolidation run alone, then deletes
+    `frac2` more and consolidates on a low-priority stream while searches of
+    the same batch run back to back on a high-priority stream.  Returns the
+    report and the deleted ids."""
+    n = ix.n_used
+    out = {"deleted_frac": frac}
+    dele = synth.pick_live_ids(n, None, int(n * frac), seed)
+    ix.delete(torch.from_numpy(dele.view(np.int32)).cuda())
+    isdel = torch.zeros(n, dtype=torch.bool, device="cuda")
+    isdel[torch.from_numpy(dele.astype(np.int64)).cuda()] = True
+    g32, _, _ = svf.knn_tc(ix.vectors()[:n], Q, 32, "ip")
+    g = g32.long()
+    live = ~isdel[g]
+    keep = live & (torch.cumsum(live.int(), 1) <= K)
+    gt = torch.where(keep, g, torch.full_like(g, -1))
+
+    def recall():
+        ids, _ = ix.search(Q, cfg)
+        hit = (ids.long().unsqueeze(2) == gt.unsqueeze(1)).any(2)
+        return hit.float().sum().item() / (Q.shape[0] * K)
+
+    def t_search(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.search(Q, cfg, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    out["recall_before"] = recall()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out["rows_rewritten"] = ix.consolidate()
+    e1.record()
+    e1.synchronize()
+    out["seconds"] = e0.elapsed_time(e1) / 1e3
+    out["recall_after"] = recall()
+    # in the background: a second consolidation after more deletes
+    dele2 = synth.pick_live_ids(n, dele, int(n * frac2), seed + 1)
+    ix.delete(torch.from_numpy(dele2.view(np.int32)).cuda())
+    lo, hi = torch.cuda.Stream.priority_range()
+    bg, fg = torch.cuda.Stream(priority=lo), torch.cuda.Stream(priority=hi)
+    base = float(np.median([t_search(fg) for _ in range(5)]))
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ix.consolidate_begin(0, stream=bg)
+    b0.record(bg)
+    rows2 = ix.consolidate_run(stream=bg)
+    b1.record(bg)
+    during = []
+    while not b1.query() and len(during) < probes:
+        during.append(t_search(fg))
+    b1.synchronize()
+    ix.consolidate_commit(stream=bg)
+    torch.cuda.synchronize()
+    out["background"] = {"deleted_frac_more": frac2, "rows_rewritten": rows2,
+                         "seconds": b0.elapsed_time(b1) / 1e3, "search_ms_alone": base,
+                         "search_ms_during_p50": float(np.median(during)) if during else None,
+                         "searches_during": len(during),
+                         "note": "consolidation on a low-priority stream, searches of the same 10K batch on a "
+                                 "high-priority stream back to back until it ends"}
+    return out, np.union1d(dele, dele2)
 
 
 def max_over_ranks(x, dist):
@@ -697,6 +769,11 @@ def main():
                                 "public API on a batch of b queries (CUDA events, host overhead included)",
                         "by_W": {str(W): {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()}},
     }
+    # global consolidation after 20 % deletes (before the store is tiered)
+    gone = None
+    if a.consolidate:
+        out["consolidation"], gone = consolidation(svf, torch, ix, Qe, cfg)
+        log_t("consolidation", json.dumps(out["consolidation"]))
     # serving: the same index with its fp32 rows tiered behind a device cache
     # of 31 % of them (the 8 GB : 25.6 GB ratio of the 50M serving workload),
     # fp8 traversal resident, exact re-rank through the tier; an open-loop
@@ -748,7 +825,7 @@ def main():
                 out["serving_policies"][p] = r
                 log_t("serving", p, json.dumps(r))
     # deletes (1% of the index, uniformly drawn live ids) with localized repair
-    dels = torch.from_numpy(synth.pick_live_ids(a.n, None, a.n // 100, 304).view(np.int32)).cuda()
+    dels = torch.from_numpy(synth.pick_live_ids(a.n, gone, a.n // 100, 304).view(np.int32)).cuda()
     torch.cuda.synchronize()
     t_del = time.time()
     ix.delete(dels)

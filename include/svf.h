@@ -210,6 +210,42 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
  * out_newly (device int64, optional) receives the number newly deleted. */
 int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly, void *stream);
 
+/* Global consolidation (Sec. 5.2) under the multi-version mechanism of
+ * Sec. 5.3, in three calls; one consolidation at a time, not on a tiered
+ * store.
+ *   svf_consolidate_sizes: bytes of the caller's consolidation buffer
+ *     (device, 256-byte aligned, borrowed until commit / abort): a snapshot
+ *     of the graph and deletion bits, repair scratch (about 8 n_cap R bytes
+ *     plus 64 MB) and a log of log_rows inserted rows.
+ *   svf_consolidate_begin: snapshot the graph rows [0, n_used) and the
+ *     deletion bits on `stream`; from now on each svf_insert batch also logs
+ *     its new rows and their distances.  More than log_rows logged rows make
+ *     the later commit fail with SVF_ECAPACITY (the active graph stays valid).
+ *   svf_consolidate_run: on the snapshot only, so it may run on its own
+ *     stream while searches and updates continue on the active graph: every
+ *     live vertex u with at least one deleted out-neighbour takes as
+ *     candidates its live row entries, then every live entry of each deleted
+ *     neighbour's row (row order, not u, no repeats; at most `cap` in all,
+ *     R <= cap <= 512; 0: the largest cap whose candidate rows the prune
+ *     stages in shared memory, min(512, 163840 / row bytes)),
+ *     sorted by (distance, id) and reordered by the index's prune (Sec. 5.1);
+ *     if fewer than R survive, its deleted entries fill the remaining slots
+ *     in their old order.  Synchronises `stream` once (the number of rows),
+ *     then queues the rest; out_rows (host, optional) gets that number.
+ *   svf_consolidate_commit: in stream order with the updates: each logged
+ *     batch's reverse edges are applied, in order, to the consolidated tails
+ *     of targets inside the snapshot (as in svf_insert), then the consolidated
+ *     rows replace rows [0, n0) of the active graph; rows inserted since the
+ *     snapshot are kept (Sec. 5.3 incremental subgraph appending and reverse
+ *     edge integration).  Returns after the copy completes.
+ *   svf_consolidate_abort: discard a consolidation (waits for a queued run).
+ * svf_build and svf_attach discard a consolidation in progress. */
+int svf_consolidate_sizes(const svf_params *p, int64_t log_rows, size_t *bytes);
+int svf_consolidate_begin(svf_index *h, void *buf, size_t bytes, int64_t log_rows, void *stream);
+int svf_consolidate_run(svf_index *h, int32_t cap, int64_t *out_rows, void *stream);
+int svf_consolidate_commit(svf_index *h, void *stream);
+int svf_consolidate_abort(svf_index *h);
+
 /* Wait for the index's last stream and report any device-side error. */
 int svf_sync(svf_index *h);
 

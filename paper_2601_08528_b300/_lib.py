@@ -21,7 +21,8 @@ MLP_PARAMS, MLP_PACKED = 1153, 1160
 
 # every symbol include/svf.h declares
 SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "svf_attach", "svf_build", "svf_search",
-           "svf_insert", "svf_delete", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
+           "svf_insert", "svf_delete", "svf_consolidate_sizes", "svf_consolidate_begin", "svf_consolidate_run",
+           "svf_consolidate_commit", "svf_consolidate_abort", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
            "svf_encode_fp8", "svf_knn", "svf_mlp_grad", "svf_mlp_partial_floats", "svf_mlp_adam", "svf_mlp_pack",
            "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta", "svf_tier_reset",
            "svf_serve_now", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
@@ -124,6 +125,11 @@ def load() -> C.CDLL:
         "svf_search": (I32, [P, P, I64, C.POINTER(SearchParams), P, P, P]),
         "svf_insert": (I32, [P, P, I64, I32, I32, P, P]),
         "svf_delete": (I32, [P, P, I64, P, P]),
+        "svf_consolidate_sizes": (I32, [C.POINTER(Params), I64, C.POINTER(C.c_size_t)]),
+        "svf_consolidate_begin": (I32, [P, P, C.c_size_t, I64, P]),
+        "svf_consolidate_run": (I32, [P, I32, C.POINTER(C.c_int64), P]),
+        "svf_consolidate_commit": (I32, [P, P]),
+        "svf_consolidate_abort": (I32, [P]),
         "svf_sync": (I32, [P]),
         "svf_stats": (I32, [P, C.POINTER(Counters)]),
         "svf_stats_reset": (I32, [P]),

@@ -135,6 +135,7 @@ int svf_create(const svf_params *p, const svf_buffers *b, svf_index **out) {
 }
 
 int svf_destroy(svf_index *h) {
+    if (h) consol_drop(h);
     delete h;
     return SVF_OK;
 }
@@ -142,6 +143,7 @@ int svf_destroy(svf_index *h) {
 int svf_attach(svf_index *h, int64_t n_used) {
     if (!h) return fail(SVF_EINVAL, "null index");
     if (n_used < 0 || n_used > h->p.n_cap) return fail(SVF_EINVAL, "n_used out of range");
+    consol_drop(h);
     h->n_used = n_used;
     return SVF_OK;
 }
@@ -167,6 +169,7 @@ int svf_build(svf_index *h, const void *X, int64_t n, void *stream) {
                                          (long long)h->ws.max_batch);
     cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
+    consol_drop(h);
     const RowDesc P = h->prim();
     CUDA_TRY(cudaMemcpyAsync(h->b.vecs, X, (size_t)n * P.pitch, cudaMemcpyDeviceToDevice, st));
     int rc = encode_lowp(h, 0, n, st);
@@ -328,7 +331,9 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     a.out_dkey = dkeys;
     CUDA_TRY(launch_prune(a, (int)m, st));
     // 3. reverse edges into the tails of the chosen neighbours
-    CUDA_TRY(launch_reverse_patch(P, h->b.graph, R, h->b.del_bits, n0, m, rows, dkeys, head, next, h->status(), st));
+    CUDA_TRY(consol_log(h, n0, m, rows, dkeys, st));
+    CUDA_TRY(launch_reverse_patch(P, h->b.graph, R, h->b.del_bits, n0, m, rows, dkeys, n0, head, next, h->status(),
+                                  st));
     // 4. the new rows
     CUDA_TRY(cudaMemcpyAsync(h->b.graph + n0 * R, rows, (size_t)m * R * 4, cudaMemcpyDeviceToDevice, st));
     if (out_ids) CUDA_TRY(launch_iota(out_ids, m, n0, st));
@@ -346,7 +351,7 @@ int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly,
     CUDA_TRY(cudaMemsetAsync(S + kStScratch0, 0, 4 * 8, st));
     CUDA_TRY(launch_delete_mark(ids, m, h->n_used, h->b.del_bits, S, st));
     uint32_t *vl = reinterpret_cast<uint32_t *>(h->wsp(h->ws.vl));
-    CUDA_TRY(launch_delete_scan(h->b.graph, R, h->b.del_bits, h->n_used, vl, S, st));
+    CUDA_TRY(launch_delete_scan(h->b.graph, R, h->b.del_bits, h->n_used, R / 2 + 1, vl, S, st));
     unsigned long long hs[3] = {0, 0, 0};
     CUDA_TRY(cudaMemcpyAsync(hs, S + kStScratch0, sizeof hs, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -359,8 +364,8 @@ int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly,
     const int cstride = h->p.repair_c * R;
     for (int64_t v0 = 0; v0 < nvl; v0 += kDeleteChunk) {
         const int64_t nv = nvl - v0 < kDeleteChunk ? nvl - v0 : kDeleteChunk;
-        CUDA_TRY(launch_delete_gather(P, h->b.graph, R, h->b.del_bits, h->n_used, h->p.repair_c, vl, v0, nv, cand,
-                                      cstride, st));
+        CUDA_TRY(launch_delete_gather(P, h->b.graph, R, h->b.del_bits, h->n_used, h->p.repair_c, kMaxRepair, vl, v0,
+                                      nv, cand, cstride, st));
         PruneArgs a{};
         a.X = P;
         a.cand = cand;

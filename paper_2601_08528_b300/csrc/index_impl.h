@@ -3,6 +3,7 @@
 // the row descriptors of the stores.
 #pragma once
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -70,6 +71,27 @@ struct Tier {
     double last_rate = 0.0, last_meanf = 0.0;
 };
 
+// Global consolidation in progress (consolidate.cu): a snapshot of the
+// graph and deletion bits, the repair's scratch, and the log of the insert
+// batches applied to the active graph since the snapshot.
+struct LoggedBatch {
+    int64_t n0, m, off;  // first new id, rows, offset in the log (rows)
+};
+struct Consol {
+    bool on = false, ran = false, overflow = false;
+    int64_t n0 = 0;           // rows in the snapshot
+    uint32_t *snap = nullptr; // [n_cap][R]
+    uint32_t *snap_del = nullptr;
+    uint32_t *vl = nullptr;   // rows to rewrite
+    uint32_t *newrows = nullptr;
+    uint64_t *cand = nullptr;
+    uint32_t *log_rows = nullptr, *log_dkeys = nullptr;  // [log_cap][R]
+    unsigned long long *ctr = nullptr;                    // private scan counters
+    int64_t log_cap = 0, log_used = 0, rewritten = 0;
+    std::vector<LoggedBatch> batches;
+    cudaEvent_t done = nullptr;  // end of the run on its stream
+};
+
 }  // namespace svf
 
 struct svf_index {
@@ -80,6 +102,7 @@ struct svf_index {
     uint64_t repaired = 0;
     cudaStream_t last = nullptr;
     svf::Tier tier;
+    svf::Consol cons;
     unsigned long long *status() const { return reinterpret_cast<unsigned long long *>(b.status); }
     uint8_t *wsp(size_t off) const { return reinterpret_cast<uint8_t *>(b.workspace) + off; }
     svf::RowDesc prim() const {
@@ -135,3 +158,12 @@ struct svf_index {
         return t;
     }
 };
+
+namespace svf {
+// Global consolidation hooks (consolidate.cu): the insert path logs each
+// batch's new rows while a consolidation is in progress; build, attach and
+// destroy drop a consolidation in progress.
+cudaError_t consol_log(svf_index *h, int64_t n0, int64_t m, const uint32_t *rows, const uint32_t *dkeys,
+                       cudaStream_t st);
+void consol_drop(svf_index *h);
+}  // namespace svf

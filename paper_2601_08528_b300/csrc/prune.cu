@@ -151,7 +151,7 @@ cudaError_t launch_prune(const PruneArgs &a, int max_lists, cudaStream_t st) {
     if (a.cand_stride > MAXC) return cudaErrorInvalidValue;
     if (max_lists <= 0) return cudaSuccess;
     const int m = a.cand_stride;
-    bool stage = a.mode == SVF_PRUNE_RNG && (size_t)m * a.X.nchunk * 16 <= 160 * 1024;
+    bool stage = a.mode == SVF_PRUNE_RNG && (size_t)m * a.X.nchunk * 16 <= (size_t)kPruneStageBytes;
     size_t smem = prune_smem(a.X.nchunk, false) + (stage ? (size_t)m * a.X.nchunk * 16 : 0);
     const int cap = sm_count() * 64;
     int grid = max_lists < cap ? max_lists : cap;

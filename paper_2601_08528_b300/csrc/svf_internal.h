@@ -98,6 +98,8 @@ cudaError_t launch_keys_to_out(const uint64_t *keys, int64_t nq, int kin, int ko
 // Neighbour reordering (prune.cu).  For each vertex v_i (i < nv) the sorted
 // candidate keys cand[i][0..ncand) (PAD-terminated) are reordered into
 // out_rows[i][0..R).  nbr: graph rows consulted by RANK (width nbr_w).
+constexpr int kPruneStageBytes = 160 * 1024;  // candidate rows the prune stages in shared memory
+
 struct PruneArgs {
     RowDesc X;
     const uint64_t *cand;

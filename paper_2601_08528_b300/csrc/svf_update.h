@@ -9,17 +9,19 @@ namespace svf {
 
 constexpr int kMaxRepair = 512;  // candidates of one localized repair (c * R)
 
+// Reverse edges of the new rows n0 .. n0+m-1 into the tail halves of their
+// targets; targets >= tmax are skipped (an insert passes tmax = n0).
 cudaError_t launch_reverse_patch(const RowDesc &X, uint32_t *graph, int R, const uint32_t *del, int64_t n0, int64_t m,
-                                 const uint32_t *rows, const uint32_t *dkeys, int32_t *head, int32_t *next,
-                                 unsigned long long *status, cudaStream_t st);
+                                 const uint32_t *rows, const uint32_t *dkeys, int64_t tmax, int32_t *head,
+                                 int32_t *next, unsigned long long *status, cudaStream_t st);
 cudaError_t launch_iota(uint32_t *out, int64_t m, int64_t base, cudaStream_t st);
 cudaError_t launch_delete_mark(const uint32_t *ids, int64_t m, int64_t n_used, uint32_t *del,
                                unsigned long long *status, cudaStream_t st);
-cudaError_t launch_delete_scan(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, uint32_t *vl,
-                               unsigned long long *status, cudaStream_t st);
+cudaError_t launch_delete_scan(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, int min_del,
+                               uint32_t *vl, unsigned long long *status, cudaStream_t st);
 cudaError_t launch_delete_gather(const RowDesc &X, const uint32_t *graph, int R, const uint32_t *del, int64_t n_used,
-                                 int c, const uint32_t *vl, int64_t v0, int64_t nv, uint64_t *cand, int cstride,
-                                 cudaStream_t st);
+                                 int c, int cap, const uint32_t *vl, int64_t v0, int64_t nv, uint64_t *cand,
+                                 int cstride, cudaStream_t st);
 cudaError_t launch_delete_finalize(uint32_t *graph, int R, const uint32_t *del, const uint32_t *vl, int64_t nv,
                                    const uint32_t *newrows, cudaStream_t st);
 

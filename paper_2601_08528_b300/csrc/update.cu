@@ -15,11 +15,11 @@
 namespace svf {
 
 // ---------------------------------------------------------------- insert
-__global__ void rev_link_kernel(const uint32_t *rows, int64_t nreq, int32_t *head, int32_t *next) {
+__global__ void rev_link_kernel(const uint32_t *rows, int64_t nreq, int64_t tmax, int32_t *head, int32_t *next) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nreq) return;
     uint32_t u = rows[i];
-    if (u == kEmpty) return;
+    if (u == kEmpty || (int64_t)u >= tmax) return;
     next[i] = atomicExch(head + u, (int32_t)i);
 }
 
@@ -27,13 +27,13 @@ __global__ void rev_link_kernel(const uint32_t *rows, int64_t nreq, int32_t *hea
 // target's list owns the target and rewrites the target's tail half.
 template <int DT>
 __global__ void rev_merge_kernel(const RowDesc X, uint32_t *graph, int R, const uint32_t *del, int64_t n0,
-                                 const uint32_t *rows, const uint32_t *dkeys, int64_t nreq, const int32_t *head,
-                                 const int32_t *next, unsigned long long *status) {
+                                 const uint32_t *rows, const uint32_t *dkeys, int64_t nreq, int64_t tmax,
+                                 const int32_t *head, const int32_t *next, unsigned long long *status) {
     const int lane = threadIdx.x & 31, sub = lane & 7, team = lane >> 3;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= nreq) return;
     const uint32_t u = rows[i];
-    if (u == kEmpty || head[u] != (int32_t)i) return;
+    if (u == kEmpty || (int64_t)u >= tmax || head[u] != (int32_t)i) return;
     const int H = R / 2, TL = R - R / 2;
     uint32_t *row = graph + (int64_t)u * R;
     // live tail entries with their distances to u
@@ -74,11 +74,11 @@ __global__ void rev_merge_kernel(const RowDesc X, uint32_t *graph, int R, const 
     if (lane == 0) atomicAdd(status + kStRevTargets, 1ull);
 }
 
-__global__ void rev_reset_kernel(const uint32_t *rows, int64_t nreq, int32_t *head) {
+__global__ void rev_reset_kernel(const uint32_t *rows, int64_t nreq, int64_t tmax, int32_t *head) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nreq) return;
     uint32_t u = rows[i];
-    if (u != kEmpty) head[u] = -1;
+    if (u != kEmpty && (int64_t)u < tmax) head[u] = -1;
 }
 
 __global__ void iota_kernel(uint32_t *out, int64_t m, int64_t base) {
@@ -87,17 +87,18 @@ __global__ void iota_kernel(uint32_t *out, int64_t m, int64_t base) {
 }
 
 cudaError_t launch_reverse_patch(const RowDesc &X, uint32_t *graph, int R, const uint32_t *del, int64_t n0, int64_t m,
-                                 const uint32_t *rows, const uint32_t *dkeys, int32_t *head, int32_t *next,
-                                 unsigned long long *status, cudaStream_t st) {
+                                 const uint32_t *rows, const uint32_t *dkeys, int64_t tmax, int32_t *head,
+                                 int32_t *next, unsigned long long *status, cudaStream_t st) {
     const int64_t nreq = m * R;
     if (nreq == 0) return cudaSuccess;
-    rev_link_kernel<<<(unsigned)((nreq + 255) / 256), 256, 0, st>>>(rows, nreq, head, next);
+    rev_link_kernel<<<(unsigned)((nreq + 255) / 256), 256, 0, st>>>(rows, nreq, tmax, head, next);
     const unsigned g = (unsigned)((nreq * 32 + 255) / 256);
     if (X.dtype == SVF_U8)
-        rev_merge_kernel<SVF_U8><<<g, 256, 0, st>>>(X, graph, R, del, n0, rows, dkeys, nreq, head, next, status);
+        rev_merge_kernel<SVF_U8><<<g, 256, 0, st>>>(X, graph, R, del, n0, rows, dkeys, nreq, tmax, head, next, status);
     else
-        rev_merge_kernel<SVF_F32><<<g, 256, 0, st>>>(X, graph, R, del, n0, rows, dkeys, nreq, head, next, status);
-    rev_reset_kernel<<<(unsigned)((nreq + 255) / 256), 256, 0, st>>>(rows, nreq, head);
+        rev_merge_kernel<SVF_F32><<<g, 256, 0, st>>>(X, graph, R, del, n0, rows, dkeys, nreq, tmax, head, next,
+                                                     status);
+    rev_reset_kernel<<<(unsigned)((nreq + 255) / 256), 256, 0, st>>>(rows, nreq, tmax, head);
     return cudaGetLastError();
 }
 
@@ -126,9 +127,10 @@ __global__ void del_mark_kernel(const uint32_t *ids, int64_t m, uint32_t *del, u
     }
 }
 
-// Warp per row: live rows with more than R/2 deleted entries join V^L.
-__global__ void del_scan_kernel(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, uint32_t *vl,
-                                unsigned long long *status) {
+// Warp per row: live rows with at least min_del deleted entries join V^L
+// (the localized repair: more than R/2; global consolidation: 1).
+__global__ void del_scan_kernel(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, int min_del,
+                                uint32_t *vl, unsigned long long *status) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -140,7 +142,7 @@ __global__ void del_scan_kernel(const uint32_t *graph, int R, const uint32_t *de
             uint32_t t = graph[u * R + s + lane];
             nd += __popc(__ballot_sync(kFull, t != kEmpty && is_deleted(del, t)));
         }
-        if (2 * nd > R && lane == 0) {
+        if (nd >= min_del && lane == 0) {
             unsigned long long p = atomicAdd(status + kStScratch0 + 2, 1ull);
             vl[p] = (uint32_t)u;
         }
@@ -148,10 +150,12 @@ __global__ void del_scan_kernel(const uint32_t *graph, int R, const uint32_t *de
 }
 
 // Warp per V^L vertex: candidate list (live row entries, then the first c
-// new live entries of each deleted neighbour's row), distances, sorted keys.
+// new live entries of each deleted neighbour's row, at most cap in all;
+// cap >= R), distances, sorted keys.
 template <int DT>
 __global__ void del_gather_kernel(const RowDesc X, const uint32_t *graph, int R, const uint32_t *del, int64_t n_used,
-                                  int c, const uint32_t *vl, int64_t v0, int64_t nv, uint64_t *cand, int cstride) {
+                                  int c, int cap, const uint32_t *vl, int64_t v0, int64_t nv, uint64_t *cand,
+                                  int cstride) {
     extern __shared__ __align__(16) uint8_t sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, team = lane >> 3, sub = lane & 7;
     const int HB = 10;  // 1024-slot id table per warp (<= 512 candidates)
@@ -202,18 +206,18 @@ __global__ void del_gather_kernel(const RowDesc X, const uint32_t *graph, int R,
         if (p == kEmpty || (int64_t)p >= n_used || !is_deleted(del, p)) continue;
         const uint32_t *prow = graph + (int64_t)p * R;
         int taken = 0;
-        for (int s = 0; s < R && taken < c; s += 32) {
+        for (int s = 0; s < R && taken < c && n < cap; s += 32) {
             uint32_t w = prow[s + lane];
             bool ok = w != kEmpty && (int64_t)w < n_used && !is_deleted(del, w) && w != u;
             uint32_t mm = __match_any_sync(kFull, ok ? w : kEmpty);
             ok = ok && (mm & lt) == 0 && !ht_has(w);
             uint32_t b = __ballot_sync(kFull, ok);
             int rk = __popc(b & lt);
-            if (ok && taken + rk < c) {
+            if (ok && taken + rk < c && n + rk < cap) {
                 ht_put(w);
                 list[n + rk] = w;
             }
-            int add = min(__popc(b), c - taken);
+            int add = min(__popc(b), min(c - taken, cap - n));
             n += add;
             taken += add;
             __syncwarp();
@@ -272,28 +276,31 @@ cudaError_t launch_delete_mark(const uint32_t *ids, int64_t m, int64_t n_used, u
     return cudaGetLastError();
 }
 
-cudaError_t launch_delete_scan(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, uint32_t *vl,
-                               unsigned long long *status, cudaStream_t st) {
+cudaError_t launch_delete_scan(const uint32_t *graph, int R, const uint32_t *del, int64_t n_used, int min_del,
+                               uint32_t *vl, unsigned long long *status, cudaStream_t st) {
     if (n_used == 0) return cudaSuccess;
     const int64_t cap = (int64_t)sm_count() * 64;
     int64_t warps = n_used < cap ? n_used : cap;
-    del_scan_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(graph, R, del, n_used, vl, status);
+    del_scan_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(graph, R, del, n_used, min_del, vl,
+                                                                            status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_delete_gather(const RowDesc &X, const uint32_t *graph, int R, const uint32_t *del, int64_t n_used,
-                                 int c, const uint32_t *vl, int64_t v0, int64_t nv, uint64_t *cand, int cstride,
-                                 cudaStream_t st) {
+                                 int c, int cap, const uint32_t *vl, int64_t v0, int64_t nv, uint64_t *cand,
+                                 int cstride, cudaStream_t st) {
     if (nv == 0) return cudaSuccess;
     const int wpb = 4;
     const size_t smem = (size_t)wpb * ((1 << 10) + 2 * kMaxRepair) * 4;
     const unsigned g = (unsigned)((nv + wpb - 1) / wpb);
     if (X.dtype == SVF_U8) {
         cudaFuncSetAttribute(del_gather_kernel<SVF_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        del_gather_kernel<SVF_U8><<<g, wpb * 32, smem, st>>>(X, graph, R, del, n_used, c, vl, v0, nv, cand, cstride);
+        del_gather_kernel<SVF_U8><<<g, wpb * 32, smem, st>>>(X, graph, R, del, n_used, c, cap, vl, v0, nv, cand,
+                                                              cstride);
     } else {
         cudaFuncSetAttribute(del_gather_kernel<SVF_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        del_gather_kernel<SVF_F32><<<g, wpb * 32, smem, st>>>(X, graph, R, del, n_used, c, vl, v0, nv, cand, cstride);
+        del_gather_kernel<SVF_F32><<<g, wpb * 32, smem, st>>>(X, graph, R, del, n_used, c, cap, vl, v0, nv, cand,
+                                                               cstride);
     }
     return cudaGetLastError();
 }

@@ -161,6 +161,43 @@ class Index:
         L.check(L.load().svf_delete(self._h, _ptr(ids), ids.numel(), _ptr(newly), _stream(stream)))
         return int(newly.item())
 
+    # ------------------------------------------------------------ global consolidation
+    def consolidate_begin(self, log_rows: int = 1_000_000, stream=None) -> None:
+        """Snapshot the graph for a global consolidation (svf_consolidate_begin);
+        up to log_rows inserted rows may be logged until the commit."""
+        lib = L.load()
+        nbytes = C.c_size_t(0)
+        L.check(lib.svf_consolidate_sizes(C.byref(self.params), log_rows, C.byref(nbytes)))
+        buf = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=self.device)
+        L.check(lib.svf_consolidate_begin(self._h, _ptr(buf), nbytes.value, log_rows, _stream(stream)))
+        self._cons_buf = buf  # borrowed by the library until commit / abort
+
+    def consolidate_run(self, cap: int = 0, stream=None) -> int:
+        """Consolidate the snapshot (may run on its own stream; cap: most
+        candidates per row, 0 = automatic); returns the number of rows it
+        rewrites."""
+        rows = C.c_int64(0)
+        L.check(L.load().svf_consolidate_run(self._h, cap, C.byref(rows), _stream(stream)))
+        return int(rows.value)
+
+    def consolidate_commit(self, stream=None) -> None:
+        """Merge the consolidated snapshot into the active graph."""
+        try:
+            L.check(L.load().svf_consolidate_commit(self._h, _stream(stream)))
+        finally:
+            self._cons_buf = None
+
+    def consolidate_abort(self) -> None:
+        L.check(L.load().svf_consolidate_abort(self._h))
+        self._cons_buf = None
+
+    def consolidate(self, cap: int = 0, stream=None) -> int:
+        """begin + run + commit on one stream; returns the rewritten rows."""
+        self.consolidate_begin(0, stream)
+        rows = self.consolidate_run(cap, stream)
+        self.consolidate_commit(stream)
+        return rows
+
     # ------------------------------------------------------------ tiered store
     def enable_tier(self, M: int, qcap: int = 16384, promote_batch: int = 2048, sweep: int = 4, alpha: float = 0.6,
                     beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp") -> None:
