@@ -226,8 +226,7 @@ int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly,
  *     live vertex u with at least one deleted out-neighbour takes as
  *     candidates its live row entries, then every live entry of each deleted
  *     neighbour's row (row order, not u, no repeats; at most `cap` in all,
- *     R <= cap <= 512; 0: the largest cap whose candidate rows the prune
- *     stages in shared memory, min(512, 163840 / row bytes)),
+ *     R <= cap <= 512, 0 meaning 512),
  *     sorted by (distance, id) and reordered by the index's prune (Sec. 5.1);
  *     if fewer than R survive, its deleted entries fill the remaining slots
  *     in their old order.  Synchronises `stream` once (the number of rows),
