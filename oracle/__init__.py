@@ -68,6 +68,7 @@ def lib():
             "orc_insert": (None, [S, I64, I64, P, I32, P, I32, I32, U64, I32, P, P]),
             "orc_delete": (I64, [S, I64, P, I32, P, P, I64, I32, I32, P, P]),
             "orc_consolidate": (I64, [S, I64, P, I32, P, I32, I32, P]),
+            "orc_consolidate_rows": (I64, [S, I64, P, I32, P, I32, I32, P, I64, P, P]),
             "orc_reverse_patch": (None, [S, P, I32, P, I64, I64, P, I64, P]),
             "orc_threads": (I32, []),
             "orc_set_threads": (None, [I32]),
@@ -285,6 +286,23 @@ def consolidate(store: Store, n0: int, graph: np.ndarray, delbits: np.ndarray, c
     if nrep < 0:
         raise ValueError("cap must be >= R")
     return int(nrep), gap[:n0]
+
+
+def consolidate_rows(store: Store, n0: int, graph: np.ndarray, delbits: np.ndarray, only, cap: int = 512,
+                     mode: int = PRUNE_RNG):
+    """The consolidated rows of the vertices `only` (graph unchanged).
+    Returns (rows [len(only)][R], rows_gap [len(only)])."""
+    graph = np.ascontiguousarray(graph, dtype=np.uint32)
+    only = np.ascontiguousarray(only, dtype=np.uint32)
+    R = graph.shape[1]
+    out = np.zeros((len(only), R), dtype=np.uint32)
+    gap = np.zeros(max(len(only), 1), dtype=np.float64)
+    st = store.c()
+    rc = lib().orc_consolidate_rows(C.byref(st), n0, _p(graph), R, _p(delbits), cap, mode, _p(only), len(only),
+                                    _p(out), _p(gap))
+    if rc < 0:
+        raise ValueError("cap must be >= R")
+    return out, gap[:len(only)]
 
 
 def reverse_patch(store: Store, graph: np.ndarray, delbits: np.ndarray | None, n0: int, rows: np.ndarray, tmax: int):

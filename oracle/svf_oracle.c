@@ -954,14 +954,17 @@ void orc_insert(const orc_store *X, int64_t n0, int64_t m, uint32_t *graph, int3
    all; sorted by (dist(u, .), id); reordered by prune_core (N_out from the
    snapshot); if fewer than R survive, u's deleted entries fill the remaining
    slots in their original order (then EMPTY).  Reads only snap, writes the
-   new rows into graph.  Returns the number of rewritten rows. */
+   new rows into graph.  With `only`, just the rows only[0 .. n_only) are
+   considered and row i of graph / rows_gap stands for vertex only[i].
+   Returns the number of rewritten rows. */
 static int64_t repair_rows(const orc_store *X, int64_t n_used, uint32_t *graph, const uint32_t *snap, int32_t R,
                            const uint32_t *del, int32_t c, int32_t min_del, int32_t cap, int32_t mode,
-                           double *rows_gap) {
+                           double *rows_gap, const uint32_t *only, int64_t n_only) {
     int d = X->d;
     int64_t nrep = 0;
+    const int64_t count = only ? n_only : n_used;
     if (rows_gap)
-        for (int64_t u = 0; u < n_used; u++) rows_gap[u] = INFINITY;
+        for (int64_t i = 0; i < count; i++) rows_gap[i] = INFINITY;
 #pragma omp parallel reduction(+ : nrep)
     {
         double *xa = (double *)malloc(sizeof(double) * d);
@@ -969,7 +972,8 @@ static int64_t repair_rows(const orc_store *X, int64_t n_used, uint32_t *graph, 
         ent *cd = (ent *)malloc(sizeof(ent) * cap);
         uint32_t *out = (uint32_t *)malloc(sizeof(uint32_t) * R);
 #pragma omp for schedule(dynamic, 64)
-        for (int64_t u = 0; u < n_used; u++) {
+        for (int64_t i = 0; i < count; i++) {
+            const int64_t u = only ? (int64_t)only[i] : i;
             if (is_deleted(del, (uint32_t)u)) continue;
             const uint32_t *row = snap + u * R;
             int nd = 0;
@@ -1016,9 +1020,9 @@ static int64_t repair_rows(const orc_store *X, int64_t n_used, uint32_t *graph, 
             int w = nc < R ? nc : R;
             for (int r = 0; r < R && w < R; r++)
                 if (row[r] != ORC_EMPTY && is_deleted(del, row[r])) out[w++] = row[r];
-            uint32_t *dst = graph + u * R;
+            uint32_t *dst = graph + i * R;
             memcpy(dst, out, sizeof(uint32_t) * R);
-            if (rows_gap) rows_gap[u] = g;
+            if (rows_gap) rows_gap[i] = g;
             nrep++;
         }
         free(xa);
@@ -1056,7 +1060,7 @@ int64_t orc_delete(const orc_store *X, int64_t n_used, uint32_t *graph, int32_t 
         }
     uint32_t *snap = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n_used > 0 ? n_used : 1) * R);
     memcpy(snap, graph, sizeof(uint32_t) * (size_t)n_used * R);
-    int64_t nrep = repair_rows(X, n_used, graph, snap, R, del, c, R / 2 + 1, R + c * R, mode, rows_gap);
+    int64_t nrep = repair_rows(X, n_used, graph, snap, R, del, c, R / 2 + 1, R + c * R, mode, rows_gap, NULL, 0);
     free(snap);
     if (out_repaired) *out_repaired = nrep;
     return newly;
@@ -1075,9 +1079,21 @@ int64_t orc_consolidate(const orc_store *X, int64_t n0, uint32_t *graph, int32_t
     if (cap < R) return -1; /* u's own live entries always fit */
     uint32_t *snap = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n0 > 0 ? n0 : 1) * R);
     memcpy(snap, graph, sizeof(uint32_t) * (size_t)n0 * R);
-    int64_t nrep = repair_rows(X, n0, graph, snap, R, del, R, 1, cap, mode, rows_gap);
+    int64_t nrep = repair_rows(X, n0, graph, snap, R, del, R, 1, cap, mode, rows_gap, NULL, 0);
     free(snap);
     return nrep;
+}
+
+/* orc_consolidate for the rows only[0 .. n_only) alone, from the unchanged
+   graph (read only): out_rows[i] = the consolidated row of vertex only[i]
+   (its current row when it is deleted or names no deleted vertex); rows_gap
+   per listed row.  For sampled checks of a large graph.  -1 for cap < R. */
+int64_t orc_consolidate_rows(const orc_store *X, int64_t n0, const uint32_t *graph, int32_t R, const uint32_t *del,
+                             int32_t cap, int32_t mode, const uint32_t *only, int64_t n_only, uint32_t *out_rows,
+                             double *rows_gap) {
+    if (cap < R) return -1;
+    for (int64_t i = 0; i < n_only; i++) memcpy(out_rows + i * R, graph + (int64_t)only[i] * R, sizeof(uint32_t) * R);
+    return repair_rows(X, n0, out_rows, graph, R, del, R, 1, cap, mode, rows_gap, only, n_only);
 }
 
 /* Reverse Edge Integration (Sec. 5.3): the logged reverse edges of one insert

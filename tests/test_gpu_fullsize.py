@@ -5,12 +5,14 @@ compute one at a time, and by properties that hold at any size.
   (exact build of 200,000 rows, then inserts of the rest); 10,000 queries
   searched in the benchmark's launch configuration (L = 64, T = 72: its
   cheapest point at recall@10 >= 0.95 for every form), plain FP32, and BF16 /
-  FP8 traversal + exact FP32 re-rank; a sample of the queries is searched by
-  the FP64 oracle on the same graph.
+  FP8 traversal + exact FP32 re-rank, and the benchmark's small-batch
+  configuration (8 warps per query, T = 12); a sample of the queries is
+  searched by the FP64 oracle on the same graph.
 * u8, 1M x 128 uint8 squared L2, R = 64: the GPU's exact build checked row
   by row on sampled vertices (exact 128-NN + prune by the oracle), sampled
-  searches bit-exact, and one insert batch of 10,000 vectors compared over the
-  whole graph with the oracle's insert of the same batch.
+  searches bit-exact, one insert batch of 10,000 vectors compared over the
+  whole graph with the oracle's insert of the same batch, and a global
+  consolidation after 20 % deletes checked bit-exact on sampled rows.
 """
 import numpy as np
 import pytest
@@ -93,6 +95,20 @@ def test_unit96_10M_lowp_rerank_search_sampled(svf, orc, unit96, prec):
     P.check_fp32(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], ref, X, Q[qs], "ip")
 
 
+def test_unit96_10M_multi_warp_sampled(svf, orc, unit96):
+    # the benchmark's small-batch configuration: 8 warps per query (8 parents
+    # per iteration), fp8 traversal + exact re-rank, T = 12
+    X, ix, g, Q = unit96
+    L, T, W = 64, 12, 8
+    ids, dist = ix.search(torch.from_numpy(Q).cuda(),
+                          svf.SearchConfig(k=10, L=L, T=T, precision="fp8", rerank=True, seed=SEED, W=W))
+    qs = sample(NQ, 48, 14)
+    lst = orc.Store.from_vectors(X, "ip", dtype="fp8")
+    o = orc.search(lst, N96, g, None, Q[qs], 10, L, T, SEED, want_pool=True, W=W)
+    st = orc.Store.from_vectors(X, "ip")
+    P.check_fp32(ids.cpu().numpy()[qs], dist.cpu().numpy()[qs], P.rerank_ref(orc, st, Q[qs], o, 10), X, Q[qs], "ip")
+
+
 # ---------------------------------------------------------------- uint8, 1M x 128, R = 64
 N8, R8, B8 = 1_000_000, 64, 10_000
 
@@ -141,3 +157,28 @@ def test_u8_1M_insert_batch_whole_graph(svf, orc, u8):
     bad = np.where((got != want).any(1))[0]
     assert len(bad) == 0, f"{len(bad)} rows differ, e.g. {bad[:5]}"
     graph_invariants(got, N8 + B8)
+
+
+def test_u8_1M_consolidation_rows_sampled(svf, orc, u8):
+    # 20 % deletes (with the localized repair), then a global consolidation of
+    # the whole graph on the GPU; sampled rows bit-exact against the oracle's
+    # consolidation of the same snapshot
+    X, ix, _ = u8
+    n = ix.n_used
+    dele = synth.pick_live_ids(n, None, n // 5, 41)
+    ix.delete(torch.from_numpy(dele.view(np.int32)).cuda())
+    snap = P.as_u32(ix.graph[:n].cpu().numpy()).astype(np.uint32)
+    bits = orc.bitset(n, dele)
+    isdel = np.zeros(n + 1, bool)
+    isdel[dele.astype(np.int64)] = True
+    named = ~isdel[:n] & isdel[np.where(snap == orc.EMPTY, n, snap)].any(1)
+    rows = ix.consolidate()
+    assert rows == named.sum()
+    got = P.as_u32(ix.graph[:n].cpu().numpy()).astype(np.uint32)
+    rng = np.random.default_rng(42)
+    vs = np.concatenate([rng.choice(np.where(named)[0], 24, replace=False),
+                         rng.choice(np.where(~named)[0], 8, replace=False)]).astype(np.uint32)
+    st = orc.Store.from_vectors(X[:n], "l2")
+    want, _ = orc.consolidate_rows(st, n, snap, bits, vs)
+    np.testing.assert_array_equal(got[vs], want)
+    graph_invariants(got, n)

@@ -366,6 +366,21 @@ def test_consolidate_hand_worked(orc):
     assert (newly, rep) == (1, 0) and loc.tolist() == g["graph"]
 
 
+def test_consolidate_rows_equals_the_whole_graph_pass(orc):
+    # the sampled form gives the rows of the whole pass, from the unchanged graph
+    n, R = 1500, 16
+    X = synth.sample("u8", n, 97)
+    st = orc.Store.from_vectors(X, "l2")
+    g, _ = orc.build_graph(st, R)
+    bits = orc.bitset(n, np.random.default_rng(98).choice(n, n // 4, replace=False))
+    only = np.random.default_rng(99).choice(n, 60, replace=False).astype(np.uint32)
+    before = g.copy()
+    rows, _ = orc.consolidate_rows(st, n, g, bits, only, cap=200)
+    np.testing.assert_array_equal(g, before)
+    orc.consolidate(st, n, g, bits, cap=200)
+    np.testing.assert_array_equal(rows, g[only])
+
+
 def test_reverse_edge_replay_hand_worked(orc):
     g, st, n0, bits = _consolidate_case(orc)
     rows = np.array([g["new_row"]], dtype=np.uint32)
