@@ -331,10 +331,10 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     """Open-loop Poisson stream at `rate` requests/s for `duration` s through
     the continuous-batching server: 90:9:1 search:insert:delete requests,
     batch sizes floor(exp(U[0, ln max_batch])), query components ~ Zipf(s).
-    small = (b, cfg_small): search batches of at most b queries run with
-    cfg_small (several warps per query).  Returns latency percentiles (ms)
-    per op over the requests that arrived after `warm` s, query and insert
-    throughput, and cache counters."""
+    small = [(b, cfg_b), ...] in ascending b: a search batch of sz queries
+    runs with the cfg of the first b >= sz (several warps per query), else
+    with cfg.  Returns latency percentiles (ms) per op over the requests that
+    arrived after `warm` s, query and insert throughput, and cache counters."""
     rng = np.random.default_rng(seed)
     m = synth.MIXTURES[mix]
     arr, ops, sizes = [], [], []
@@ -372,7 +372,7 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     t0 = svf.Server.now() + 0.5
     for tag, (ta, op, sz) in enumerate(zip(arr, ops, sizes)):
         if op == 0:
-            c = small[1] if small and sz <= small[0] else cfg
+            c = next((cb for b, cb in small if sz <= b), cfg) if small else cfg
             srv.search(tag, Qall[qo:qo + sz], c, ids_out[qo:qo + sz], d_out[qo:qo + sz], t_arrival=t0 + ta)
             qo += sz
         elif op == 1:
@@ -391,7 +391,7 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     srv.stop()
     st = ix.stats()
     lat = {0: [], 1: [], 2: []}
-    by_size = {"le16": [], "gt16": []}  # search latency by batch size
+    by_size = {"1-16": [], "17-256": [], "257-2048": []}  # search latency by batch size
     done_q = done_i = 0
     t_first, t_last = None, None
     for c in comps:
@@ -399,7 +399,7 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
             continue
         lat[c["op"]].append(1e3 * (c["t_done"] - c["t_arrival"]))
         if c["op"] == 0:
-            by_size["le16" if c["count"] <= 16 else "gt16"].append(lat[0][-1])
+            by_size["1-16" if c["count"] <= 16 else "17-256" if c["count"] <= 256 else "257-2048"].append(lat[0][-1])
         if c["op"] == 0:
             done_q += c["count"]
         elif c["op"] == 1:
@@ -541,7 +541,7 @@ def serve_main(a, svf, torch, log_t):
     # batches of up to --serve-small queries: 8 warps per query (measured before tiering)
     sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target, Ws=(1, 8)) if a.serve_small > 0 else {}
     log_t("small batches", {W: {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()})
-    small = (a.serve_small, sb[8]["cfg"]) if 8 in sb else None
+    small = [(a.serve_small, sb[8]["cfg"])] if 8 in sb else None
     slots = int(8e9 // (128 * 4))
     ix.enable_tier(M=slots, theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
     ix.release_device_store()
@@ -568,8 +568,8 @@ def serve_main(a, svf, torch, log_t):
                       "cache_rows": slots, "L": cfg.L,
                       "T": cfg.T, "recall@10": rec, "mix": "90:9:1", "batch": "log-uniform 1..2048",
                       "queries": "Zipf(1.1) over components",
-                      "small_batches": (f"batches of <= {small[0]} queries: W = 8, T = {small[1].T}" if small
-                                        else None)},
+                      "small_batches": (f"batches of <= {small[0][0]} queries: W = 8, T = {small[0][1].T}"
+                                        if small else None)},
            "small_batch": {str(W): {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()},
            "rates": res}
     if res1:
@@ -792,9 +792,12 @@ def main():
             trav = "fp32 traversal through the tier"
         else:
             trav = "fp8 traversal + exact re-rank"
-        # batches of up to 16 queries take the several-warps-per-query path
-        if a.serve_trav != "fp32" and 8 in sb:
-            sopt["small"] = (16, sb[8]["cfg"])
+        # latency-bound batches take the several-warps-per-query path: 8 warps up
+        # to 256 queries, 4 up to 640, 2 up to 1,536 (the crossovers of the
+        # one-call latency on this index: W = 8 leads up to 256 queries, W = 4
+        # at 512, W = 2 at 1,024, W = 1 from 2,048)
+        if a.serve_trav != "fp32" and all(W in sb for W in (2, 4, 8)):
+            sopt["small"] = [(256, sb[8]["cfg"]), (640, sb[4]["cfg"]), (1536, sb[2]["cfg"])]
         out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg,
                                       **sopt)
         qmix = (f"queries from a window of {win_arg[0]} components moving {win_arg[1]:g}/s" if win_arg
@@ -804,7 +807,8 @@ def main():
                                       "batches log-uniform 1..2048")
         out["serving"]["policy"] = "wavp"
         if "small" in sopt:
-            out["serving"]["small_batches"] = f"batches of <= 16 queries: W = 8, T = {sb[8]['T']}"
+            out["serving"]["small_batches"] = (f"W = 8 (T = {sb[8]['T']}) up to 256 queries, W = 4 (T = {sb[4]['T']}) "
+                                               f"up to 640, W = 2 (T = {sb[2]['T']}) up to 1,536, else W = 1")
         log_t("serving", json.dumps(out["serving"]))
         if "small" in sopt:
             # the same stream (same seed, re-tiered cache) with one warp per query throughout
