@@ -78,9 +78,9 @@ def parse():
     ap.add_argument("--consolidate", type=int, default=1,
                     help="unit96-10M: delete 20%% of the index and consolidate it (before the serving stream, "
                          "which then runs on the consolidated index); 0 skips")
-    ap.add_argument("--serve-small", type=int, default=16,
-                    help="serve128-50M: search batches of at most this many queries run with 8 warps per query "
-                         "(0: one warp per query throughout)")
+    ap.add_argument("--serve-small", type=int, default=1,
+                    help="serve128-50M: latency-bound search batches run with several warps per query, W by "
+                         "batch size from a measurement before tiering (0: one warp per query throughout)")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve128-50M: also run each rate's stream with one warp per query throughout")
     ap.add_argument("--serve-lins", type=int, default=128, help="insert search pool of the 50M build")
@@ -267,6 +267,26 @@ def consolidation(svf, torch, ix, Q, cfg, frac=0.2, frac2=0.05, seed=307, probes
                          "note": "consolidation on a low-priority stream, searches of the same 10K batch on a "
                                  "high-priority stream back to back until it ends"}
     return out, np.union1d(dele, dele2)
+
+
+def w_policy(sb, sizes=(16, 256, 1024)):
+    """Serving policy from small_batch's measurement: a batch of up to b
+    queries (b in `sizes`) takes the W with the lowest one-call latency at b;
+    larger batches keep one warp per query.  Returns [(b, cfg), ...]."""
+    out = []
+    for b in sizes:
+        key = f"b{b}_p50_ms"
+        cand = [(r[key], W) for W, r in sb.items() if key in r]
+        if not cand:
+            continue
+        _, W = min(cand)
+        if W == 1:
+            continue
+        if out and out[-1][1].W == W:
+            out[-1] = (b, out[-1][1])  # the same W over a wider range
+        else:
+            out.append((b, sb[W]["cfg"]))
+    return out
 
 
 def max_over_ranks(x, dist):
@@ -538,10 +558,10 @@ def serve_main(a, svf, torch, log_t):
             op = (cfg, r)
             break
     cfg, rec = op if op else (cfg, r)
-    # batches of up to --serve-small queries: 8 warps per query (measured before tiering)
-    sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target, Ws=(1, 8)) if a.serve_small > 0 else {}
+    # latency-bound batches: W by batch size from one-call latencies measured before tiering
+    sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target, sizes=(1, 16, 256, 1024)) if a.serve_small else {}
     log_t("small batches", {W: {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()})
-    small = [(a.serve_small, sb[8]["cfg"])] if 8 in sb else None
+    small = w_policy(sb) or None
     slots = int(8e9 // (128 * 4))
     ix.enable_tier(M=slots, theta0=2.0, promote_batch=2048, sweep=4, qcap=16384)
     ix.release_device_store()
@@ -568,8 +588,8 @@ def serve_main(a, svf, torch, log_t):
                       "cache_rows": slots, "L": cfg.L,
                       "T": cfg.T, "recall@10": rec, "mix": "90:9:1", "batch": "log-uniform 1..2048",
                       "queries": "Zipf(1.1) over components",
-                      "small_batches": (f"batches of <= {small[0][0]} queries: W = 8, T = {small[0][1].T}"
-                                        if small else None)},
+                      "small_batches": (", ".join(f"W = {c.W} (T = {c.T}) up to {b} queries" for b, c in small)
+                                        + ", else W = 1" if small else None)},
            "small_batch": {str(W): {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()},
            "rates": res}
     if res1:
@@ -728,7 +748,7 @@ def main():
     e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
     clk = clocks.stop(torch.cuda.current_device())
     # ---- latency-bound batches: several warps per query (not timed above)
-    sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target)
+    sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target, sizes=(1, 16, 256, 1024))
     log_t("small batches", {W: {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()})
 
     # ---- roofline of the search kernel (the only launch of a step)
@@ -792,12 +812,10 @@ def main():
             trav = "fp32 traversal through the tier"
         else:
             trav = "fp8 traversal + exact re-rank"
-        # latency-bound batches take the several-warps-per-query path: 8 warps up
-        # to 256 queries, 4 up to 640, 2 up to 1,536 (the crossovers of the
-        # one-call latency on this index: W = 8 leads up to 256 queries, W = 4
-        # at 512, W = 2 at 1,024, W = 1 from 2,048)
-        if a.serve_trav != "fp32" and all(W in sb for W in (2, 4, 8)):
-            sopt["small"] = [(256, sb[8]["cfg"]), (640, sb[4]["cfg"]), (1536, sb[2]["cfg"])]
+        # latency-bound batches take the several-warps-per-query path, W by
+        # batch size from the one-call latencies measured above
+        if a.serve_trav != "fp32":
+            sopt["small"] = w_policy(sb)
         out["serving"] = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg,
                                       **sopt)
         qmix = (f"queries from a window of {win_arg[0]} components moving {win_arg[1]:g}/s" if win_arg
@@ -806,11 +824,11 @@ def main():
                                       f"{tier['M'] / 1e6:.1f}M-row device cache, {trav}, {qmix}, 90:9:1 mix, "
                                       "batches log-uniform 1..2048")
         out["serving"]["policy"] = "wavp"
-        if "small" in sopt:
-            out["serving"]["small_batches"] = (f"W = 8 (T = {sb[8]['T']}) up to 256 queries, W = 4 (T = {sb[4]['T']}) "
-                                               f"up to 640, W = 2 (T = {sb[2]['T']}) up to 1,536, else W = 1")
+        if sopt.get("small"):
+            out["serving"]["small_batches"] = ", ".join(f"W = {c.W} (T = {c.T}) up to {b} queries"
+                                                        for b, c in sopt["small"]) + ", else W = 1"
         log_t("serving", json.dumps(out["serving"]))
-        if "small" in sopt:
+        if sopt.get("small"):
             # the same stream (same seed, re-tiered cache) with one warp per query throughout
             ix.reset_tier(policy="wavp", **tier)
             one = dict(sopt, small=None)
