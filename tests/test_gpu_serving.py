@@ -18,10 +18,10 @@ def svf():
     return svf
 
 
-def built(svf, mix, n, n_cap, R=32, metric="l2", seed=701, max_batch=None):
+def built(svf, mix, n, n_cap, R=32, metric="l2", seed=701, max_batch=None, lowp=()):
     X = synth.sample(mix, n_cap, seed)
     ix = svf.Index(X.shape[1], n_cap, dtype="u8" if X.dtype == np.uint8 else "f32", metric=metric, R=R,
-                   max_batch=max_batch or n)
+                   max_batch=max_batch or n, lowp=lowp)
     ix.build(torch.from_numpy(X[:n]).cuda())
     return X, ix
 
@@ -44,6 +44,24 @@ def test_tiered_search_equals_device_search(svf):
     ids2, d2 = ix.search(Q, cfg)
     assert torch.equal(ids0, ids2) and torch.equal(d0, d2)
 
+
+def test_tiered_multi_warp_and_rerank_equal_device_search(svf):
+    # several warps per query over the tiered store: traversal rows (fp32) and
+    # re-rank rows (fp8 traversal resident) read through the cache give the
+    # results of the device-resident store, and the cache counters see them
+    X, ix = built(svf, "unit96", 6000, 6000, R=32, metric="ip", lowp=("fp8",))
+    Q = torch.from_numpy(synth.sample("unit96", 300, 703)).cuda()
+    cfgs = [svf.SearchConfig(k=10, L=64, T=10, seed=3, W=4),
+            svf.SearchConfig(k=10, L=64, T=8, seed=3, W=8, precision="fp8", rerank=True)]
+    want = [ix.search(Q, c) for c in cfgs]
+    ix.enable_tier(M=600, theta0=0.5, promote_batch=256, sweep=4, qcap=4096)
+    ix.release_device_store()
+    for c, (i0, d0) in zip(cfgs, want):
+        ix.stats_reset()
+        i1, d1 = ix.search(Q, c)
+        assert torch.equal(i0, i1) and torch.equal(d0, d1)
+        s = ix.stats()
+        assert s["cache_hits"] > 0 and s["cache_misses"] > 0
 
 
 def test_promotion_follows_a_skewed_workload(svf):
