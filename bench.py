@@ -269,6 +269,12 @@ def consolidation(svf, torch, ix, Q, cfg, frac=0.2, frac2=0.05, seed=307, probes
     return out, np.union1d(dele, dele2)
 
 
+def pick_cfg(small, sz, cfg):
+    """The search config of a batch of sz queries: that of the first (b, cfg_b)
+    in `small` (ascending b) with sz <= b, else cfg."""
+    return next((cb for b, cb in small if sz <= b), cfg) if small else cfg
+
+
 def w_policy(sb, sizes=(16, 256, 1024)):
     """Serving policy from small_batch's measurement: a batch of up to b
     queries (b in `sizes`) takes the W with the lowest one-call latency at b;
@@ -392,7 +398,7 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     t0 = svf.Server.now() + 0.5
     for tag, (ta, op, sz) in enumerate(zip(arr, ops, sizes)):
         if op == 0:
-            c = next((cb for b, cb in small if sz <= b), cfg) if small else cfg
+            c = pick_cfg(small, sz, cfg)
             srv.search(tag, Qall[qo:qo + sz], c, ids_out[qo:qo + sz], d_out[qo:qo + sz], t_arrival=t0 + ta)
             qo += sz
         elif op == 1:
