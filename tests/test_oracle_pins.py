@@ -305,6 +305,11 @@ def test_search_w_parents_hand_worked(orc):
         assert r["pool_ids"][0].tolist() == c["pool"], c
         assert (r["iters"][0], r["evals"][0]) == (c["parents"], c["evals"]), c
         assert r["ids"][0].tolist() == c["pool"]
+    bits = orc.bitset(n, g["deleted"])
+    for c in g["cases_deleted"]:
+        r = orc.search(st, n, graph, bits, q, L, L, c["T"], g["seed"], want_pool=True, W=c["W"])
+        assert r["pool_ids"][0].tolist() == c["pool"], c
+        assert (r["iters"][0], r["evals"][0]) == (c["parents"], c["evals"]), c
 
 
 @pytest.mark.parametrize("W", [2, 4, 8])
