@@ -638,3 +638,63 @@ def test_trace_features_and_labels(orc):
         if tl >= 1:
             cut = orc.search(st, n, g, None, Q[qi:qi + 1], 10, 64, tl, 1)
             assert set(cut["ids"][0]) != set(plain["ids"][qi])
+
+
+def test_trace_features_hand_worked(orc):
+    """All 16 learned-stop features of a hand-worked trace on the 12-point
+    line graph (f5 population std, f6 admitted over R, f8 new top-k ids, f9
+    iterations since the last top-k change, f11 parent rank, f13 drop of d1,
+    f14 next parent against dk, f15 the running average of f6)."""
+    line = _golden("search_wparents_hand.json")
+    g = _golden("search_trace_hand.json")
+    n = line["n"]
+    X = np.zeros((n, 4), dtype=np.float32)
+    X[:, 0] = np.arange(n)
+    st = orc.Store.from_vectors(X, "l2")
+    graph = np.array(line["graph"], dtype=np.uint32)
+    q = np.array([line["query"]], dtype=np.float32)
+    r = orc.search_ex(st, n, graph, None, q, g["k"], g["L"], g["T"], g["seed"], trace=True)
+    assert r["n_feat"][0] == g["n_feat"] and r["t_last"][0] == g["t_last"]
+    want = np.array(g["feat"])
+    np.testing.assert_allclose(r["feat"][0, :g["n_feat"]], want, rtol=1e-12, atol=1e-14)
+    assert not r["feat"][0, g["n_feat"]:].any()
+    # the pools the features were read from
+    for t, pool in enumerate(g["pool_after"]):
+        p = orc.search(st, n, graph, None, q, g["L"], g["L"], t + 1, g["seed"], want_pool=True)
+        assert p["pool_ids"][0].tolist() == pool
+    # label y_t = (t >= t_last): a search cut after t_last + 1 iterations has the final top k
+    full = orc.search(st, n, graph, None, q, g["k"], g["L"], g["T"], g["seed"])
+    cut = orc.search(st, n, graph, None, q, g["k"], g["L"], g["t_last"] + 1, g["seed"])
+    assert cut["ids"].tolist() == full["ids"].tolist()
+
+
+# ---------------------------------------------------------------- WAVP (Sec. 4.3, Eq. 2, Alg. 2)
+@pytest.mark.parametrize("case", [0, 1])
+def test_wavp_round_hand_worked(orc, case):
+    """One maintenance round worked by hand: candidate order by descending
+    F_lambda with an id tie, an empty slot taken first, referenced slots
+    passed over and cleared, a victim tie decided by slot, and (case 1) the
+    second sweep when too few slots were unreferenced."""
+    g = _golden("wavp_round_hand.json")
+    c = g["cases"][case]
+    n, M = c["n"], c["M"]
+    owner = np.array(c["owner"], dtype=np.int32)
+    ref = np.array(c["ref"], dtype=np.uint8)
+    map_ = np.full(n, -1, dtype=np.int32)
+    for s, o in enumerate(owner):
+        if o >= 0:
+            map_[o] = s
+    freq = np.zeros(n, dtype=np.uint32)
+    for x, f in c["freq"].items():
+        freq[int(x)] = f
+    ein = np.zeros(n, dtype=np.uint32)
+    for x, e in c["ein"].items():
+        ein[int(x)] = e
+    p, e = orc.wavp_round(map_, owner, ref, freq, ein, c["queue"], c["B"], c["hand"], c["W"], g["alpha"], g["beta"])
+    assert (p, e) == (c["promoted"], c["evicted"])
+    assert owner.tolist() == c["owner_after"]
+    assert ref.tolist() == c["ref_after"]
+    want = np.full(n, -1, dtype=np.int32)
+    for x, s in c["mapped_after"].items():
+        want[int(x)] = s
+    np.testing.assert_array_equal(map_, want)
