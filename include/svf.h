@@ -408,8 +408,12 @@ int svf_knn_tc(const float *X, int64_t n, int32_t d, int32_t metric, const float
  * current) and caches it; make that first call before any stream capture.
  * All calls share the array, which keeps the last call's keys: calls that
  * overlap on the GPU (different streams, devices sharing nothing else) race
- * and must be serialised by the caller.  The call allocates nothing.  Errors
- * are described by svf_knn_static_error(). */
+ * and must be serialised by the caller.  The call allocates nothing.  The
+ * cached address belongs to the device's primary context: after that context
+ * is destroyed (cudaDeviceReset) it is stale, as is every other device
+ * pointer the caller held, and the library must be reloaded.  Errors are
+ * described by svf_knn_static_error() and, like every other call's, by
+ * svf_last_error(). */
 int svf_knn_static(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, const void *Q, int64_t nq,
                    const int64_t *self, int32_t k, uint32_t *out_ids, void *out_dist, void *stream);
 int64_t svf_knn_static_capacity(void);

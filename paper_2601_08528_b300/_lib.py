@@ -26,7 +26,8 @@ SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "s
            "svf_encode_fp8", "svf_knn", "svf_mlp_grad", "svf_mlp_partial_floats", "svf_mlp_adam", "svf_mlp_pack",
            "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta", "svf_tier_reset",
            "svf_serve_now", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
-           "svf_serve_stop", "svf_knn_tc_scratch_bytes", "svf_knn_tc", "svf_wait_limit", "svf_selftest_wait_timeout"]
+           "svf_serve_stop", "svf_knn_tc_scratch_bytes", "svf_knn_tc", "svf_wait_limit", "svf_selftest_wait_timeout",
+           "svf_knn_static", "svf_knn_static_capacity", "svf_knn_static_error"]
 
 
 class Params(C.Structure):
@@ -156,6 +157,9 @@ def load() -> C.CDLL:
         "svf_knn_tc": (I32, [P, I64, I32, I32, P, I64, I32, P, C.c_size_t, P, P, C.POINTER(C.c_int64), P]),
         "svf_wait_limit": (C.c_uint32, []),
         "svf_selftest_wait_timeout": (I32, [C.c_uint32, P, C.POINTER(C.c_double), P]),
+        "svf_knn_static": (I32, [P, I64, I32, I32, I32, P, I64, P, I32, P, P, P]),
+        "svf_knn_static_capacity": (I64, []),
+        "svf_knn_static_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -11,10 +11,14 @@
 // every GPU that loads the library holds it until the process exits.  Host
 // code cannot use the array's name as a device address (on the host it names
 // a host-side shadow), so the device address is looked up once per device
-// with cudaGetSymbolAddress, with that device current, and cached.
+// with cudaGetSymbolAddress, with that device current, and cached.  The
+// cached address belongs to the device's primary context: after that context
+// is torn down (cudaDeviceReset) it is stale, like every other device pointer
+// the caller held.
 #include <cstdio>
 #include <mutex>
 
+#include "index_impl.h"
 #include "svf_internal.h"
 
 namespace {
@@ -28,9 +32,11 @@ uint64_t *g_addr[kMaxDevices] = {};
 
 thread_local char g_msg[256];
 
+// The message goes to svf_knn_static_error() and, like every other entry
+// point's, to svf_last_error().
 int fail_static(int code, const char *msg) {
     snprintf(g_msg, sizeof g_msg, "svf_knn_static: %s", msg);
-    return code;
+    return svf::fail(code, "%s", g_msg);
 }
 
 // Device address of the scratch array on the current device (set-up on the

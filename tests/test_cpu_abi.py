@@ -74,3 +74,29 @@ def test_oracle_and_library_share_no_code():
         if f.endswith((".py", ".c")):
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2601_08528_b300" not in txt and "svf.h" not in txt, f
+
+
+def test_static_knn_validation_before_any_cuda_call(lib):
+    """svf_knn_static answers bad arguments with SVF_EINVAL and a message on
+    both error paths, before it touches a device (none exists here)."""
+    from paper_2601_08528_b300 import _lib as L
+    cap = lib.svf_knn_static_capacity()
+    assert cap == 1 << 20
+    P = C.c_void_p(16)  # never dereferenced: every case below fails validation first
+    cases = [
+        dict(n=0), dict(d=100), dict(d=0), dict(k=0), dict(k=129), dict(dtype=L.BF16), dict(metric=5),
+        dict(nq=cap // 128 + 1, k=128), dict(nq=cap // 10 + 1), dict(X=None), dict(Q=None), dict(out=None), dict(nq=-1),
+    ]
+    for c in cases:
+        a = dict(X=P, n=100, d=16, dtype=L.F32, metric=L.L2, Q=P, nq=4, k=10, out=P)
+        a.update(c)
+        rc = lib.svf_knn_static(a["X"], a["n"], a["d"], a["dtype"], a["metric"], a["Q"], a["nq"], None, a["k"],
+                                a["out"], None, None)
+        assert rc == L.SVF_EINVAL, c
+        msg = lib.svf_knn_static_error()
+        assert msg.startswith(b"svf_knn_static: "), c
+        assert lib.svf_last_error() == msg, c
+    assert b"exceeds" in (lib.svf_knn_static(P, 100, 16, 0, 0, P, cap // 128 + 1, None, 128, P, None, None)
+                          and lib.svf_knn_static_error())
+    # an empty batch is a no-op that needs no pointers
+    assert lib.svf_knn_static(None, 100, 16, 0, 0, None, 0, None, 10, None, None, None) == L.SVF_OK

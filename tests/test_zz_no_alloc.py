@@ -4,7 +4,8 @@ Callers that cannot call cudaMalloc (a plugin inside a framework that owns
 the device memory, a latency-critical loop) use svf_knn_static, whose scratch
 is a fixed device array inside the library.  Its output must equal svf_knn's
 (which uses a caller-allocated buffer) on two calls in a row: the second call
-reuses the array and must not see the first call's keys.
+reuses the array and must not see the first call's keys.  A warmed-up call
+must leave both the device's free memory and torch's allocator unchanged.
 """
 import ctypes as C
 
@@ -18,49 +19,100 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _static_fn():
+def _lib():
     import paper_2601_08528_b300 as svf
-    lib = svf.load()
-    f = lib.svf_knn_static
-    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
-    f.restype = I32
-    f.argtypes = [P, I64, I32, I32, I32, P, I64, P, I32, P, P, P]
-    lib.svf_knn_static_error.restype = C.c_char_p
-    lib.svf_knn_static_capacity.restype = I64
-    return svf, lib, f
+    from paper_2601_08528_b300 import _lib as L
+    return svf, L, L.load()
 
 
 def _p(t):
-    return C.c_void_p(t.data_ptr())
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _static(lib, X, Q, k, metric, self_ids=None):
+    nq = Q.shape[0]
+    dt = 1 if X.dtype == torch.uint8 else 0
+    ids = torch.full((nq, k), -7, dtype=torch.int32, device="cuda")
+    dist = torch.full((nq, k), -7, dtype=torch.int32 if dt else torch.float32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.svf_knn_static(_p(X), X.shape[0], X.shape[1], dt, 1 if metric == "ip" else 0, _p(Q), nq, _p(self_ids),
+                            k, _p(ids), _p(dist), stream)
+    assert rc == 0, lib.svf_knn_static_error()
+    return ids, dist
+
+
+def _same(a, b, u8):
+    np.testing.assert_array_equal(a[0].cpu().numpy(), b[0].cpu().numpy())
+    if u8:
+        np.testing.assert_array_equal(a[1].cpu().numpy(), b[1].cpu().numpy())
+    else:
+        np.testing.assert_allclose(a[1].cpu().numpy(), b[1].cpu().numpy(), rtol=1e-5, atol=1e-6)
 
 
 @pytest.mark.parametrize("mix,metric,k", [("u8", "l2", 10), ("unit96", "ip", 32)])
 def test_static_knn_matches_allocating_knn_twice(mix, metric, k):
-    svf, lib, f = _static_fn()
+    svf, L, lib = _lib()
     assert lib.svf_knn_static_capacity() == 1 << 20
     X = torch.from_numpy(synth.sample(mix, 6000, 501)).cuda()
-    dt = 1 if mix == "u8" else 0
-    mt = 1 if metric == "ip" else 0
-    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call, (nq, seed) in enumerate([(333, 502), (97, 503)]):
         Q = torch.from_numpy(synth.sample(mix, nq, seed)).cuda()
-        ref_ids, ref_d = svf.knn(X, Q, k, metric)
-        ids = torch.full((nq, k), -7, dtype=torch.int32, device="cuda")
-        dist = torch.empty_like(ref_d)
-        rc = f(_p(X), X.shape[0], X.shape[1], dt, mt, _p(Q), nq, None, k, _p(ids), _p(dist), stream)
-        assert rc == 0, lib.svf_knn_static_error()
+        ref = svf.knn(X, Q, k, metric)
+        got = _static(lib, X, Q, k, metric)
         torch.cuda.synchronize()
-        np.testing.assert_array_equal(ids.cpu().numpy(), ref_ids.cpu().numpy(), err_msg=f"call {call}")
-        if dt == 1:
-            np.testing.assert_array_equal(dist.cpu().numpy(), ref_d.cpu().numpy())
-        else:
-            np.testing.assert_allclose(dist.cpu().numpy(), ref_d.cpu().numpy(), rtol=1e-5, atol=1e-6)
+        _same(got, ref, mix == "u8")
+
+
+def test_static_knn_with_self_exclusion_and_at_capacity():
+    """Rows excluded by `self` (each query is a row of the store), and a
+    batch that fills the fixed array exactly (nq * k == capacity)."""
+    svf, L, lib = _lib()
+    cap = lib.svf_knn_static_capacity()
+    X = torch.from_numpy(synth.sample("u8", 9000, 511)).cuda()
+    sel = torch.arange(0, 9000, 7, dtype=torch.int64, device="cuda")[:1000]
+    Q = X[sel].contiguous()
+    ref = svf.knn(X, Q, 16, "l2", self_ids=sel)
+    got = _static(lib, X, Q, 16, "l2", self_ids=sel)
+    torch.cuda.synchronize()
+    _same(got, ref, True)
+    assert not (got[0].long() == sel[:, None]).any()
+    k = 128
+    nq = cap // k
+    Xf = torch.from_numpy(synth.sample("tiny", 3000, 512)).cuda()
+    Qf = torch.from_numpy(synth.sample("tiny", nq, 513)).cuda()
+    ref = svf.knn(Xf, Qf, k, "l2")
+    got = _static(lib, Xf, Qf, k, "l2")
+    torch.cuda.synchronize()
+    _same(got, ref, False)
+
+
+def test_static_knn_allocates_nothing():
+    svf, L, lib = _lib()
+    X = torch.from_numpy(synth.sample("tiny", 5000, 521)).cuda()
+    Q = torch.from_numpy(synth.sample("tiny", 700, 522)).cuda()
+    ids = torch.empty((700, 10), dtype=torch.int32, device="cuda")
+    dist = torch.empty((700, 10), dtype=torch.float32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        assert lib.svf_knn_static(_p(X), 5000, 128, 0, 0, _p(Q), 700, None, 10, _p(ids), _p(dist), stream) == 0
+
+    call()  # warm-up: module load and the one-time address lookup
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == (alloc0, reserved0)
+    assert free1 == free0
 
 
 def test_static_knn_rejects_oversized_batches():
-    svf, lib, f = _static_fn()
+    svf, L, lib = _lib()
     X = torch.zeros((100, 16), dtype=torch.float32, device="cuda")
     Q = torch.zeros((1, 16), dtype=torch.float32, device="cuda")
     ids = torch.empty((1, 128), dtype=torch.int32, device="cuda")
-    rc = f(_p(X), 100, 16, 0, 0, _p(Q), (1 << 20) // 128 + 1, None, 128, _p(ids), None, None)
+    rc = lib.svf_knn_static(_p(X), 100, 16, 0, 0, _p(Q), (1 << 20) // 128 + 1, None, 128, _p(ids), None, None)
     assert rc == -1 and b"exceeds" in lib.svf_knn_static_error()
+    assert lib.svf_last_error() == lib.svf_knn_static_error()
