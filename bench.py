@@ -9,13 +9,15 @@ Its graph is built on the GPU: an exact 2R-NN + prune build of the first
 200,000 vectors, then batched inserts of the rest (Sec. 5.1 insert path).
 
 Forms compared (each at the cheapest swept (L, T) reaching recall@10 >= 0.95
-against exact ground truth): plain FP32 traversal; BF16 / FP8 traversal with
+against exact ground truth on held-out queries): plain FP32 traversal; BF16 / FP8 traversal with
 an exact FP32 re-rank of the final pool; the same with the learned early stop
 (trained here on traces of 200,000 training queries).  `value` is the QPS of
 the fastest form; one step = one search launch over the 10,000-query batch.
 
-`--impl reference` times the CPU oracle (FP64, all host cores) on a bounded
-sample of the same batch, same graph, same (L, T).
+Every form's (L, T) is chosen on 20,000 held-out calibration queries and
+then measured on the 10,000 timed queries.  `--impl reference` times the CPU
+oracle (FP64, all host cores) on the same batch, same graph, same (L, T):
+one pass over all 10,000 queries per step.
 """
 from __future__ import annotations
 
@@ -57,7 +59,6 @@ def parse():
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--ntrain", type=int, default=200_000)
     ap.add_argument("--target", type=float, default=0.95)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=500.0, help="requests/s of the serving stream (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
     ap.add_argument("--workload", default="unit96-10M", choices=["unit96-10M", "serve128-50M"])
@@ -83,6 +84,9 @@ def parse():
                          "batch size from a measurement before tiering (0: one warp per query throughout)")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve128-50M: also run each rate's stream with one warp per query throughout")
+    ap.add_argument("--raw-rates", default="500,2000,5000,10000",
+                    help="request rates of the read-after-write consistency stream (empty: skip)")
+    ap.add_argument("--raw-seconds", type=float, default=1.0)
     ap.add_argument("--serve-lins", type=int, default=128, help="insert search pool of the 50M build")
     ap.add_argument("--serve-tins", type=int, default=96, help="insert search iterations of the 50M build")
     return ap.parse_args()
@@ -353,14 +357,18 @@ def train_stops(torch, svf, ix, Qtr, gt_cal, ncal, precisions):
 
 # ---------------------------------------------------------------- serving
 def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zipf_s=1.1, max_inflight=8,
-                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048, window=None, small=None):
+                 n_streams=4, maintain_every=128, L_ins=64, T_ins=32, max_batch=2048, window=None, small=None,
+                 consistency="snapshot"):
     """Open-loop Poisson stream at `rate` requests/s for `duration` s through
     the continuous-batching server: 90:9:1 search:insert:delete requests,
     batch sizes floor(exp(U[0, ln max_batch])), query components ~ Zipf(s).
     small = [(b, cfg_b), ...] in ascending b: a search batch of sz queries
     runs with the cfg of the first b >= sz (several warps per query), else
-    with cfg.  Returns latency percentiles (ms) per op over the requests that
-    arrived after `warm` s, query and insert throughput, and cache counters."""
+    with cfg.  consistency: the server's mode ("snapshot": searches read the
+    last completed update's state and never wait; "read-after-write";
+    "barrier").  Returns latency percentiles (ms) per op over the requests
+    that arrived after `warm` s, query and insert throughput, and cache
+    counters."""
     rng = np.random.default_rng(seed)
     m = synth.MIXTURES[mix]
     arr, ops, sizes = [], [], []
@@ -390,7 +398,8 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
     k = cfg.k
     ids_out = torch.empty((max(nq, 1), k), dtype=torch.int32, device="cuda")
     d_out = torch.empty((max(nq, 1), k), dtype=torch.int32 if m.dtype == "u8" else torch.float32, device="cuda")
-    srv = svf.Server(ix, max_inflight=max_inflight, n_streams=n_streams, maintain_every=maintain_every)
+    srv = svf.Server(ix, max_inflight=max_inflight, n_streams=n_streams, maintain_every=maintain_every,
+                     consistency=consistency, shadow_rows=max_batch * ix.R)
     ix.stats_reset()
     qo, io = 0, 0
     n_used = ix.n_used
@@ -444,7 +453,48 @@ def serve_stream(svf, torch, ix, mix, X_ins, rate, duration, warm, seed, cfg, zi
                                           for k, v in by_size.items()},
            "cache_hit_rate": (st["cache_hits"] / max(1, st["cache_hits"] + st["cache_misses"]))
            if st["cache_hits"] + st["cache_misses"] else None,
-           "promoted": st["promoted"], "evicted": st["evicted"]}
+           "promoted": st["promoted"], "evicted": st["evicted"], "consistency": consistency}
+    return out
+
+
+def read_after_write(svf, torch, ix, X_new, rates, cfg, seconds=2.0, batch=10, seed=320):
+    """The consistency experiment of Table 3 (Sec. 6): an open-loop Poisson
+    stream of requests, half inserts of `batch` new vectors and half searches
+    for the vectors the previous insert added, under each consistency mode.
+    Recall@1 = fraction of those searches whose nearest result is the vector
+    itself; p99 over all requests.  Returns {mode: {rate: {...}}}."""
+    out = {}
+    used = 0
+    for mode in ("read-after-write", "snapshot"):
+        out[mode] = {}
+        for rate in rates:
+            rng = np.random.default_rng(seed)
+            arr = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds)))
+            n_pairs = min(len(arr) // 2, (X_new.shape[0] - used) // batch, (ix.n_cap - ix.n_used) // batch)
+            if n_pairs <= 0:
+                continue
+            xs = torch.from_numpy(X_new[used:used + n_pairs * batch]).cuda()
+            used += n_pairs * batch
+            ids = torch.empty((n_pairs * batch, cfg.k), dtype=torch.int32, device="cuda")
+            dd = torch.empty((n_pairs * batch, cfg.k), dtype=torch.float32, device="cuda")
+            srv = svf.Server(ix, max_inflight=8, n_streams=4, consistency=mode, shadow_rows=batch * ix.R)
+            base = ix.n_used
+            t0 = svf.Server.now() + 0.2
+            for i in range(n_pairs):
+                sl = slice(i * batch, (i + 1) * batch)
+                srv.insert(2 * i, xs[sl], L_ins=64, T_ins=32, t_arrival=t0 + arr[2 * i])
+                srv.search(2 * i + 1, xs[sl], cfg, ids[sl], dd[sl], t_arrival=t0 + arr[2 * i + 1])
+            srv.drain(600)
+            comps = srv.poll(1 << 20)
+            srv.stop()
+            want = torch.arange(base, base + n_pairs * batch, device="cuda", dtype=torch.int64)
+            r1 = (ids[:, 0].long() == want).float().mean().item()
+            lat = [1e3 * (c["t_done"] - c["t_arrival"]) for c in comps]
+            slat = [1e3 * (c["t_done"] - c["t_arrival"]) for c in comps if c["op"] == 0]
+            out[mode][str(rate)] = {"recall@1": r1, "p99_ms": float(np.percentile(lat, 99)),
+                                    "search_p50_ms": float(np.percentile(slat, 50)),
+                                    "search_p99_ms": float(np.percentile(slat, 99)), "pairs": n_pairs}
+            log(f"  read-after-write stream {mode} rate {rate}: {out[mode][str(rate)]}")
     return out
 
 
@@ -520,34 +570,55 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------- CPU oracle timing
-def oracle_qps(X, graph_np, Q, L, T, seconds, form="fp32"):
-    """The oracle timed on the host cores for `form`: fixed-T FP64 search over
+class OracleTimer:
+    """The oracle timed on the host cores in `form`: fixed-T FP64 search over
     the fp32 rows, or over the bf16 / fp8 copy followed by the exact FP64
-    re-rank of the final pool (the same steps as the GPU form).  A sample of
-    the queries sized to about `seconds`; returns (queries/s, sample, threads)."""
-    import oracle as orc
-    prec = form.split("+")[0]
-    st = orc.Store.from_vectors(X, "ip")
-    trav = st if prec == "fp32" else orc.Store.from_vectors(X, "ip", dtype=prec)
-    n = X.shape[0]
+    re-rank of the final pool (the same steps as the GPU form).  The stores
+    are laid out once; `rate(Q)` times one pass over the queries Q and returns
+    (queries/s, threads)."""
 
-    def run(q):
-        o = orc.search(trav, n, graph_np, None, q, K, L, T, 0x5F0C, want_pool=prec != "fp32")
-        if prec != "fp32":  # exact re-rank of the final pool
-            pd = orc.dist_ids(st, q, o["pool_ids"])
+    def __init__(self, X, graph_np, L, T, form="fp32"):
+        import oracle as orc
+        self.orc = orc
+        self.prec = form.split("+")[0]
+        self.st = orc.Store.from_vectors(X, "ip")
+        self.trav = self.st if self.prec == "fp32" else orc.Store.from_vectors(X, "ip", dtype=self.prec)
+        self.n, self.g, self.L, self.T = X.shape[0], graph_np, L, T
+
+    def run(self, q):
+        o = self.orc.search(self.trav, self.n, self.g, None, q, K, self.L, self.T, 0x5F0C,
+                            want_pool=self.prec != "fp32")
+        if self.prec != "fp32":  # exact re-rank of the final pool
+            pd = self.orc.dist_ids(self.st, q, o["pool_ids"])
             for i in range(len(q)):
                 np.lexsort((o["pool_ids"][i], pd[i]))[:K]
         return o
 
-    m = 16
-    t = time.time()
-    run(Q[:m])
-    dt = time.time() - t
-    m2 = int(min(Q.shape[0], max(m, seconds / max(dt / m, 1e-6))))
-    t = time.time()
-    run(Q[:m2])
-    dt = time.time() - t
-    return m2 / dt, m2, orc.threads()
+    def rate(self, Q):
+        t = time.time()
+        self.run(Q)
+        return Q.shape[0] / (time.time() - t), self.orc.threads()
+
+
+def select_points(torch, ix, forms, grid, target, learned, Qcal, gt_cal, Qe, gt):
+    """Operating points chosen on held-out calibration queries, measured on the
+    evaluation queries: for each form the cheapest swept (L, T) whose recall@10
+    over Qcal reaches `target`, then its recall and QPS over Qe (queries the
+    choice never saw)."""
+    from paper_2601_08528_b300.learned import recall_at_k
+    pts, chosen = sweep(torch, ix, Qcal, gt_cal, forms, grid, target, learned)
+    best = {}
+    for name, p in chosen.items():
+        cfg = p["cfg"]
+        ix.stats_reset()
+        ids, _ = ix.search(Qe, cfg)
+        its = ix.stats()["search_iters"] / Qe.shape[0]
+        sec = time_search(torch, ix, Qe, cfg)
+        best[name] = {"form": name, "L": p["L"], "T": p["T"], "recall": recall_at_k(ids, gt), "qps": Qe.shape[0] / sec,
+                      "cfg": cfg, "iters": its, "recall_cal": p["recall"]}
+        log(f"  chosen {name:16s} L={p['L']:3d} T={p['T']:3d} recall cal {p['recall']:.4f} eval "
+            f"{best[name]['recall']:.4f} qps={best[name]['qps']:,.0f}")
+    return pts, best
 
 
 # ---------------------------------------------------------------- serving workload (50M)
@@ -648,7 +719,7 @@ def main():
     policies = [p for p in a.serve_policies.split(",") if p]
     # capacity for the inserts of every serving stream: the main one, the
     # one-warp-per-query rerun and the placement ablation
-    ix = build_index(svf, torch, X, log_t, streams=2 + len(policies))
+    ix = build_index(svf, torch, X, log_t, streams=5 + len(policies))
     Xd = ix.vectors()[:a.n]
     Qe = torch.from_numpy(Qe_np).cuda()
     gt = exact_knn(svf, Xd, Qe, K, "ip")
@@ -657,23 +728,30 @@ def main():
 
     grid = [(64, 32), (64, 64), (64, 72), (64, 80), (64, 96), (128, 48), (128, 56), (128, 64), (128, 72), (128, 80),
             (128, 96), (256, 96), (256, 128)]
+    # held-out calibration queries (the first tenth of the training queries):
+    # every operating point is chosen on them, never on the timed batch
+    ncal = a.ntrain // 10
+    Qtr_np = synth.sample_chunked("unit96", a.ntrain, 401)
+    Qcal = torch.from_numpy(Qtr_np[:ncal]).cuda()
+    gt_cal = exact_knn(svf, Xd, Qcal, K, "ip")
     if a.impl == "reference":
         # the oracle on the headline form (fp8 traversal + exact re-rank) at its
-        # cheapest swept operating point with recall@10 >= target
+        # cheapest operating point with recall@10 >= target on the calibration
+        # queries; each step is one pass over the whole timed batch
         form = "fp8+rerank"
         base = [(form, svf.SearchConfig(k=K, precision="fp8", rerank=True))]
-        _, best = sweep(torch, ix, Qe, gt, base, grid, a.target, {})
+        _, best = select_points(torch, ix, base, grid, a.target, {}, Qcal, gt_cal, Qe, gt)
         op = best.get(form) or {"L": 256, "T": 192}
         g_np = ix.graph[:a.n].cpu().numpy().view(np.uint32)
-        steps = []
-        m_used, cores = 0, 0
+        timer = OracleTimer(X, g_np, op["L"], op["T"], form)
+        steps, cores = [], 0
         for s in range(a.warmup + a.steps):
-            q, m_used, cores = oracle_qps(X, g_np, Qe_np, op["L"], op["T"], a.cpu_seconds / max(1, a.steps), form)
+            q, cores = timer.rate(Qe_np)
             if s >= a.warmup:
                 steps.append(q)
         v = statistics.median(steps)
-        sample = (f"{m_used} of {a.nq} queries per step, FP64 fixed-T search over the fp8 copy + exact re-rank at "
-                  f"L={op['L']} T={op['T']} on the GPU-built graph")
+        sample = (f"all {a.nq} queries of the batch per step (median of {a.steps} steps), FP64 fixed-T search over "
+                  f"the fp8 copy + exact re-rank at L={op['L']} T={op['T']} on the GPU-built graph")
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
                "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -685,18 +763,16 @@ def main():
         return 0
 
     # learned stop: traces of the plain search of training queries
-    Qtr = torch.from_numpy(synth.sample_chunked("unit96", a.ntrain, 401)).cuda()
-    ncal = a.ntrain // 10
-    gt_cal = exact_knn(svf, Xd, Qtr[:ncal], K, "ip")
+    Qtr = torch.from_numpy(Qtr_np).cuda()
     nets = train_stops(torch, svf, ix, Qtr, gt_cal, ncal, ["bf16", "fp8"])
-    del Qtr
+    del Qtr, Qtr_np
     log_t("stop networks")
     forms = [("fp32", svf.SearchConfig(k=K)),
              ("bf16+rerank", svf.SearchConfig(k=K, precision="bf16", rerank=True)),
              ("fp8+rerank", svf.SearchConfig(k=K, precision="fp8", rerank=True)),
              ("bf16+rerank+stop", svf.SearchConfig(k=K, precision="bf16", rerank=True)),
              ("fp8+rerank+stop", svf.SearchConfig(k=K, precision="fp8", rerank=True))]
-    pts, best = sweep(torch, ix, Qe, gt, forms, grid, a.target, nets)
+    pts, best = select_points(torch, ix, forms, grid, a.target, nets, Qcal, gt_cal, Qe, gt)
     log_t("sweep")
     if not best:
         raise SystemExit("no form reached the recall target")
@@ -797,8 +873,10 @@ def main():
                    "L": cfg.L, "T": cfg.T, "tau": getattr(cfg, "tau", None) if cfg.mlp is not None else None,
                    "recall@10": win["recall"], "l2": f"inputs larger than L2 ({a.n * 96 * 4 / 1e9:.1f} GB store, {a.n * R * 4 / 1e9:.1f} GB graph)",
                    "graph": f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins=64, T_ins=48)"},
-        "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "L": v["L"], "T": v["T"], "iters": v["iters"]}
-                  for k, v in best.items()},
+        "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "recall@10_calibration": v["recall_cal"],
+                      "L": v["L"], "T": v["T"], "iters": v["iters"]} for k, v in best.items()},
+        "operating_point": "each form's cheapest swept (L, T) with recall@10 >= target on 20,000 held-out "
+                           "calibration queries; recall and QPS measured on the 10,000 timed queries",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(form, cfg.L, cfg.T),
                      "peak_source": src,
@@ -852,6 +930,24 @@ def main():
             out["serving"]["small_batches"] = ", ".join(f"W = {c.W} (T = {c.T}) up to {b} queries"
                                                         for b, c in sopt["small"]) + ", else W = 1"
         log_t("serving", json.dumps(out["serving"]))
+        # the same stream (same seed, re-tiered cache) under the other two
+        # consistency modes: a search waits for every update submitted before
+        # it, or every update waits for the searches and runs alone
+        for mode in ("read-after-write", "barrier"):
+            ix.reset_tier(policy="wavp", **tier)
+            r = serve_stream(svf, torch, ix, "unit96", X_ins, a.serve_rate, a.serve_seconds, 1.0, 306, cfg,
+                             **dict(sopt, consistency=mode))
+            out["serving_" + mode.replace("-", "_")] = r
+            log_t("serving", mode, json.dumps(r))
+        if a.raw_rates:
+            # Table 3's experiment: half inserts of 10 vectors, half searches for them
+            ix.reset_tier(policy="wavp", **tier)
+            X_raw = synth.sample_chunked("unit96", 200_000, 308)
+            out["read_after_write"] = read_after_write(svf, torch, ix, X_raw,
+                                                       [float(x) for x in a.raw_rates.split(",")], cfg,
+                                                       seconds=a.raw_seconds)
+            out["read_after_write"]["note"] = ("requests alternate an insert of 10 new vectors and a search for "
+                                               "them (Poisson arrivals); recall@1 = the vector itself returned first")
         if sopt.get("small"):
             # the same stream (same seed, re-tiered cache) with one warp per query throughout
             ix.reset_tier(policy="wavp", **tier)
@@ -885,10 +981,10 @@ def main():
         # (a stop form is timed without its network, i.e. for the full T)
         hf, hc = win["form"].replace("+stop", ""), win["cfg"]
         g_np = ix.graph[:a.n].cpu().numpy().view(np.uint32)
-        qps, m, cores = oracle_qps(X, g_np, Qe_np, hc.L, hc.T, a.cpu_seconds, hf)
+        qps, cores = OracleTimer(X, g_np, hc.L, hc.T, hf).rate(Qe_np)
         out["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                               "sample": f"{m} queries, FP64 fixed-T search in the {hf} form at L={hc.L} T={hc.T} "
-                                         f"on the same graph"}
+                               "sample": f"all {a.nq} queries of the batch, FP64 fixed-T search in the {hf} form at "
+                                         f"L={hc.L} T={hc.T} on the same graph"}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

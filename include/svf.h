@@ -335,21 +335,51 @@ int svf_tier_reset(svf_index *h, const svf_tier_params *tp, void *stream);
  * Sec. 5.3 consistency).  A worker thread admits requests in submission
  * order, each no earlier than its t_arrival (svf_serve_now clock; 0 = now).
  * Searches run on n_streams streams with up to max_inflight batches on the
- * GPU at once; an insert or delete waits for the in-flight searches, runs
- * alone and advances the epoch, so each search reads exactly the state of
- * its epoch (its result equals the same search run alone on that state).
+ * GPU at once; inserts and deletes run one at a time on a dedicated update
+ * stream.  Every request completes with an epoch: for an update, its number
+ * (1, 2, ... in submission order); for a search, the number of updates whose
+ * effect it sees -- its result equals the same search run alone on the index
+ * state after exactly those updates.  `consistency` says how searches meet
+ * updates:
+ *   SVF_SERVE_BARRIER           an update waits for the in-flight searches,
+ *                               runs alone, and later searches wait for it.
+ *   SVF_SERVE_READ_AFTER_WRITE  an update runs while earlier searches are
+ *                               still on the GPU; a search sees every update
+ *                               submitted before it (its stream waits for the
+ *                               last one), the paper's "with sync" mode.
+ *   SVF_SERVE_SNAPSHOT          as above, but a search sees the updates that
+ *                               have completed when it is admitted and never
+ *                               waits for one (the paper's "without sync").
+ * The last two keep versions for the searches that overlap an update: the
+ * update copies every existing row it rewrites into a shadow row and stamps
+ * it, and stamps every vertex it deletes, so that a search of an older epoch
+ * reads the row as it was and still treats the vertex as live (vertices an
+ * update inserts have ids the older search never names).  One shadow per row
+ * is kept: update E+1 starts once every search of an epoch below E has
+ * finished.  An update that rewrites more than shadow_rows existing rows
+ * (an insert of m vectors rewrites at most m*R; a delete's repair is counted
+ * on the device) runs as a barrier instead.  `versions` is a device buffer of
+ * svf_serve_version_bytes(h, shadow_rows) bytes, borrowed until stop.
  * With a tiered store, svf_tier_maintain runs every maintain_every search
- * batches while nothing is in flight.  All request buffers are device
- * memory owned by the caller and must stay valid until the completion for
- * the request has been polled. */
+ * batches while nothing is in flight.  All request buffers are device memory
+ * owned by the caller and must stay valid until the completion for the
+ * request has been polled. */
 enum svf_op { SVF_OP_SEARCH = 0, SVF_OP_INSERT = 1, SVF_OP_DELETE = 2 };
+enum svf_consistency { SVF_SERVE_BARRIER = 0, SVF_SERVE_READ_AFTER_WRITE = 1, SVF_SERVE_SNAPSHOT = 2 };
 
 typedef struct {
     int32_t max_inflight;
     int32_t n_streams;
     int32_t maintain_every;
-    int32_t reserved0;
+    int32_t consistency;      /* svf_consistency */
+    void *versions;           /* device, svf_serve_version_bytes bytes (consistency 1 or 2), else NULL */
+    size_t versions_bytes;
+    int64_t shadow_rows;      /* existing rows one update may rewrite concurrently with searches */
 } svf_serve_cfg;
+
+/* Bytes of the version buffer for an index (row stamps, deletion stamps and
+ * two halves of shadow_rows shadow rows). */
+size_t svf_serve_version_bytes(svf_index *h, int64_t shadow_rows);
 
 typedef struct {
     int32_t op;               /* svf_op */

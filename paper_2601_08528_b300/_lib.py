@@ -25,7 +25,7 @@ SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "s
            "svf_consolidate_commit", "svf_consolidate_abort", "svf_sync", "svf_stats", "svf_stats_reset", "svf_encode_bf16",
            "svf_encode_fp8", "svf_knn", "svf_mlp_grad", "svf_mlp_partial_floats", "svf_mlp_adam", "svf_mlp_pack",
            "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta", "svf_tier_reset",
-           "svf_serve_now", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
+           "svf_serve_now", "svf_serve_version_bytes", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
            "svf_serve_stop", "svf_knn_tc_scratch_bytes", "svf_knn_tc", "svf_wait_limit", "svf_selftest_wait_timeout",
            "svf_knn_static", "svf_knn_static_capacity", "svf_knn_static_error"]
 
@@ -84,7 +84,8 @@ OP_SEARCH, OP_INSERT, OP_DELETE = 0, 1, 2
 
 class ServeCfg(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("n_streams", C.c_int32), ("maintain_every", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("consistency", C.c_int32), ("versions", C.c_void_p), ("versions_bytes", C.c_size_t),
+                ("shadow_rows", C.c_int64)]
 
 
 class Request(C.Structure):
@@ -148,6 +149,7 @@ def load() -> C.CDLL:
         "svf_tier_theta": (C.c_float, [P]),
         "svf_tier_reset": (I32, [P, C.POINTER(TierParams), P]),
         "svf_serve_now": (C.c_double, []),
+        "svf_serve_version_bytes": (C.c_size_t, [P, I64]),
         "svf_serve_start": (I32, [P, C.POINTER(ServeCfg), C.POINTER(C.c_void_p)]),
         "svf_serve_submit": (I32, [P, C.POINTER(Request)]),
         "svf_serve_poll": (I32, [P, C.POINTER(Completion), I32, C.POINTER(C.c_int32)]),

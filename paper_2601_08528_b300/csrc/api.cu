@@ -213,8 +213,10 @@ static int hash_bits_for(int L, int R, int req, int span = 1) {
 }
 
 static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search_params *sp, uint32_t *out_ids,
-                       void *out_dist, cudaStream_t st, int64_t n_used, const RowDesc &trav) {
+                       void *out_dist, cudaStream_t st, int64_t n_used, const RowDesc &trav,
+                       const VerCtx *ver = nullptr) {
     SearchArgs a{};
+    if (ver) a.ver = *ver;
     a.trav = trav;
     a.prim = h->prim();
     a.graph = h->b.graph;
@@ -250,12 +252,8 @@ static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search
     return SVF_OK;
 }
 
-int svf_search(svf_index *h, const void *Q, int64_t nq, const svf_search_params *sp, uint32_t *out_ids,
-               void *out_dist, void *stream) {
-    if (!h || !sp) return fail(SVF_EINVAL, "null index / params");
-    if (nq < 0) return fail(SVF_EINVAL, "nq < 0");
-    if (nq == 0) return SVF_OK;
-    if (!Q || !out_ids || !out_dist) return fail(SVF_EINVAL, "null Q / outputs");
+// Argument checks of a search; *trav (out) = the store the traversal reads.
+static int check_search(svf_index *h, const svf_search_params *sp, RowDesc *trav_out) {
     if (sp->L != 32 && sp->L != 64 && sp->L != 128 && sp->L != 256) return fail(SVF_EINVAL, "L must be 32/64/128/256");
     if (sp->k < 1 || sp->k > 32 || sp->k > sp->L) return fail(SVF_EINVAL, "need 1 <= k <= min(L, 32)");
     if (sp->T < 0) return fail(SVF_EINVAL, "T < 0");
@@ -274,12 +272,46 @@ int svf_search(svf_index *h, const void *Q, int64_t nq, const svf_search_params 
         return fail(SVF_EINVAL, "W must be 0, 1, 2, 4 or 8");
     if (sp->W > 1 && (sp->mlp || sp->trace_feat || sp->trace_meta))
         return fail(SVF_EINVAL, "the stop network and traces run with one warp per query (W <= 1)");
+    *trav_out = trav;
+    return SVF_OK;
+}
+
+int svf_search(svf_index *h, const void *Q, int64_t nq, const svf_search_params *sp, uint32_t *out_ids,
+               void *out_dist, void *stream) {
+    if (!h || !sp) return fail(SVF_EINVAL, "null index / params");
+    if (nq < 0) return fail(SVF_EINVAL, "nq < 0");
+    if (nq == 0) return SVF_OK;
+    if (!Q || !out_ids || !out_dist) return fail(SVF_EINVAL, "null Q / outputs");
+    RowDesc trav{};
+    if (int rc = check_search(h, sp, &trav)) return rc;
     h->last = (cudaStream_t)stream;
     return search_impl(h, Q, nq, sp, out_ids, out_dist, (cudaStream_t)stream, h->n_used, trav);
 }
 
+}  // extern "C"
+
+int svf::search_at(svf_index *h, const void *Q, int64_t nq, const svf_search_params *sp, uint32_t *out_ids,
+                   void *out_dist, cudaStream_t st, int64_t n_used, const VerCtx &ver) {
+    if (!h || !sp) return fail(SVF_EINVAL, "null index / params");
+    if (nq < 0) return fail(SVF_EINVAL, "nq < 0");
+    if (nq == 0) return SVF_OK;
+    if (!Q || !out_ids || !out_dist) return fail(SVF_EINVAL, "null Q / outputs");
+    RowDesc trav{};
+    if (int rc = check_search(h, sp, &trav)) return rc;
+    return search_impl(h, Q, nq, sp, out_ids, out_dist, st, n_used, trav, &ver);
+}
+
+extern "C" {
+
 int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_ins, uint32_t *out_ids,
                void *stream) {
+    return svf::insert_impl(h, X, m, L_ins, T_ins, out_ids, (cudaStream_t)stream, nullptr);
+}
+
+}  // extern "C"
+
+int svf::insert_impl(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_ins, uint32_t *out_ids,
+                     cudaStream_t st, const VerUpd *ver) {
     if (!h) return fail(SVF_EINVAL, "null index");
     if (m < 0) return fail(SVF_EINVAL, "m < 0");
     if (m == 0) return SVF_OK;
@@ -291,7 +323,7 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     if (L_ins != 32 && L_ins != 64 && L_ins != 128 && L_ins != 256) return fail(SVF_EINVAL, "L_ins must be 32..256");
     if (L_ins < h->p.R) return fail(SVF_EINVAL, "L_ins must be >= R");
     if (T_ins < 0) return fail(SVF_EINVAL, "T_ins < 0");
-    cudaStream_t st = (cudaStream_t)stream;
+    if (ver && m * h->p.R > ver->cap) return fail(SVF_ECAPACITY, "insert of %lld rows exceeds the shadow rows", (long long)m);
     h->last = st;
     const RowDesc P = h->prim();
     const int64_t n0 = h->n_used;
@@ -333,7 +365,7 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     // 3. reverse edges into the tails of the chosen neighbours
     CUDA_TRY(consol_log(h, n0, m, rows, dkeys, st));
     CUDA_TRY(launch_reverse_patch(P, h->b.graph, R, h->b.del_bits, n0, m, rows, dkeys, n0, head, next, h->status(),
-                                  st));
+                                  st, ver));
     // 4. the new rows
     CUDA_TRY(cudaMemcpyAsync(h->b.graph + n0 * R, rows, (size_t)m * R * 4, cudaMemcpyDeviceToDevice, st));
     if (out_ids) CUDA_TRY(launch_iota(out_ids, m, n0, st));
@@ -341,15 +373,23 @@ int svf_insert(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_
     return SVF_OK;
 }
 
+extern "C" {
+
 int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly, void *stream) {
+    return svf::delete_impl(h, ids, m, out_newly, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+}  // extern "C"
+
+int svf::delete_impl(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly, cudaStream_t st,
+                     const VerUpd *ver, const std::function<bool(int64_t)> *shadow_fits) {
     if (!h) return fail(SVF_EINVAL, "null index");
     if (m < 0 || (m > 0 && !ids)) return fail(SVF_EINVAL, "bad ids / m");
-    cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
     unsigned long long *S = h->status();
     const int R = h->p.R;
     CUDA_TRY(cudaMemsetAsync(S + kStScratch0, 0, 4 * 8, st));
-    CUDA_TRY(launch_delete_mark(ids, m, h->n_used, h->b.del_bits, S, st));
+    CUDA_TRY(launch_delete_mark(ids, m, h->n_used, h->b.del_bits, S, st, ver));
     uint32_t *vl = reinterpret_cast<uint32_t *>(h->wsp(h->ws.vl));
     CUDA_TRY(launch_delete_scan(h->b.graph, R, h->b.del_bits, h->n_used, R / 2 + 1, vl, S, st));
     unsigned long long hs[3] = {0, 0, 0};
@@ -378,10 +418,16 @@ int svf_delete(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly,
         a.out_rows = newrows + v0 * R;
         CUDA_TRY(launch_prune(a, (int)nv, st));
     }
+    // rows read by searches of the previous epoch are shadowed before they
+    // are rewritten (unless the caller has none running: too many rows)
+    if (ver && nvl > 0 && (!shadow_fits || (*shadow_fits)(nvl)))
+        CUDA_TRY(launch_stamp_rows(h->b.graph, R, vl, nvl, *ver, S, st));
     CUDA_TRY(launch_delete_finalize(h->b.graph, R, h->b.del_bits, vl, nvl, newrows, st));
     h->repaired += (uint64_t)nvl;
     return SVF_OK;
 }
+
+extern "C" {
 
 int svf_sync(svf_index *h) {
     if (!h) return fail(SVF_EINVAL, "null index");

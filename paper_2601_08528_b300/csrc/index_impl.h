@@ -3,6 +3,7 @@
 // the row descriptors of the stores.
 #pragma once
 #include <cmath>
+#include <functional>
 #include <vector>
 #include <cstdarg>
 #include <cstdio>
@@ -163,6 +164,19 @@ namespace svf {
 // Global consolidation hooks (consolidate.cu): the insert path logs each
 // batch's new rows while a consolidation is in progress; build, attach and
 // destroy drop a consolidation in progress.
+// Insert / delete with optional version stamping for searches of the
+// previous epoch that are still running (serve.cu).  shadow_fits(nvl) tells
+// whether the repair's nvl rows fit the update's shadow rows; when it returns
+// false the caller has made sure no search of an older epoch is running and
+// the rows are rewritten without shadows.
+int insert_impl(svf_index *h, const void *X, int64_t m, int32_t L_ins, int32_t T_ins, uint32_t *out_ids,
+                cudaStream_t st, const VerUpd *ver);
+int delete_impl(svf_index *h, const uint32_t *ids, int64_t m, int64_t *out_newly, cudaStream_t st, const VerUpd *ver,
+                const std::function<bool(int64_t)> *shadow_fits);
+// Search with an explicit id bound and versioned reads (serve.cu).
+int search_at(svf_index *h, const void *Q, int64_t nq, const svf_search_params *sp, uint32_t *out_ids, void *out_dist,
+              cudaStream_t st, int64_t n_used, const VerCtx &ver);
+
 cudaError_t consol_log(svf_index *h, int64_t n0, int64_t m, const uint32_t *rows, const uint32_t *dkeys,
                        cudaStream_t st);
 void consol_drop(svf_index *h);

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         const int j = j0 + lane;
         // multiply-shift range reduction of the upper 32 random bits
         const uint32_t id = __umulhi((uint32_t)(splitmix64(base ^ (uint64_t)j) >> 32), (uint32_t)a.n_used);
-        bool ok = j < ndraw && !is_deleted(a.del, id);
+        bool ok = j < ndraw && !(a.ver.row_ver ? deleted_at(a.ver, a.del, id) : is_deleted(a.del, id));
         uint32_t m = __match_any_sync(kFull, ok ? id : kEmpty);
         bool first = ok && ((m & lt_mask) == 0);
         bool acc = first && !ht_contains(ht, a.hash_bits, id);
@@ -280,10 +280,14 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         // deletion bits are read while the rows are in flight and deleted
         // ids are dropped before the merge (putting a deleted id in the
         // visited table changes nothing: it never enters the pool).
-        const uint32_t *row = a.graph + (int64_t)pid * R;
         uint32_t nb[S];
+        if (a.ver.row_ver) {
+            versioned_row<S>(a.ver, a.graph, pid, lane, nb);
+        } else {
+            const uint32_t *row = a.graph + (int64_t)pid * R;
 #pragma unroll
-        for (int s = 0; s < S; s++) nb[s] = __ldg(row + s * 32 + lane);
+            for (int s = 0; s < S; s++) nb[s] = __ldg(row + s * 32 + lane);
+        }
         int nf = 0;
 #pragma unroll
         for (int s = 0; s < S; s++) {
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
 #pragma unroll
         for (int s = 0; s < S; s++) {
             const int e = s * 32 + lane;
-            dword[s] = e < nf ? __ldg(a.del + (list[e] >> 5)) : 0u;
+            dword[s] = e < nf ? (a.ver.row_ver ? __ldcg(a.del + (list[e] >> 5)) : __ldg(a.del + (list[e] >> 5))) : 0u;
         }
         const uint32_t newflag = learn ? kNewBit : 0u;
         if (!staged_dist<DT, NCH>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb, tier, &hits, &misses)) {
@@ -312,6 +316,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         for (int s = 0; s < S; s++) {
             const int e = s * 32 + lane;
             dflag[s] = e < nf && ((dword[s] >> (list[e] & 31)) & 1u);
+            // a deletion after the search's epoch leaves the vertex live for it
+            if (dflag[s] && a.ver.row_ver) dflag[s] = ld_relaxed_u32(a.ver.del_ep + list[e]) <= a.ver.epoch;
             ndel += __popc(__ballot_sync(kFull, dflag[s]));
         }
         evals += nf - ndel;

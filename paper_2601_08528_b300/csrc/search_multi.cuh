@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
         for (int j0 = 0; j0 < ndraw && np < L && a.n_used > 0; j0 += 32) {
             const int j = j0 + lane;
             const uint32_t id = __umulhi((uint32_t)(splitmix64(base ^ (uint64_t)j) >> 32), (uint32_t)a.n_used);
-            bool ok = j < ndraw && !is_deleted(a.del, id);
+            bool ok = j < ndraw && !(a.ver.row_ver ? deleted_at(a.ver, a.del, id) : is_deleted(a.del, id));
             uint32_t m = __match_any_sync(kFull, ok ? id : kEmpty);
             bool first = ok && ((m & lt_mask) == 0);
             bool acc = first && !ht_contains(ht, a.hash_bits, id);
@@ -168,10 +168,14 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
         // ---- warp w < npar: FetchNeighbors of parent w, filter, stage, score,
         //      append the keys that can enter the pool
         if (wid < npar) {
-            const uint32_t *row = a.graph + (int64_t)ctl->par[wid] * R;
             uint32_t nb[S];
+            if (a.ver.row_ver) {
+                versioned_row<S>(a.ver, a.graph, ctl->par[wid], lane, nb);
+            } else {
+                const uint32_t *row = a.graph + (int64_t)ctl->par[wid] * R;
 #pragma unroll
-            for (int s = 0; s < S; s++) nb[s] = __ldg(row + s * 32 + lane);
+                for (int s = 0; s < S; s++) nb[s] = __ldg(row + s * 32 + lane);
+            }
             int nf = 0;
 #pragma unroll
             for (int s = 0; s < S; s++) {
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
 #pragma unroll
             for (int s = 0; s < S; s++) {
                 const int e = s * 32 + lane;
-                dword[s] = e < nf ? __ldg(a.del + (list[e] >> 5)) : 0u;
+                dword[s] = e < nf ? (a.ver.row_ver ? __ldcg(a.del + (list[e] >> 5)) : __ldg(a.del + (list[e] >> 5))) : 0u;
             }
             if (!staged_dist<DT, NCH>(stg, a.trav, list, nf, keys, 0u, lane, qf, qb, tier, &hits, &misses)) {
                 if (lane == 0) {
@@ -202,7 +206,9 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
 #pragma unroll
             for (int s = 0; s < S; s++) {
                 const int e = s * 32 + lane;
-                const bool live = e < nf && !((dword[s] >> (list[e] & 31)) & 1u);
+                bool live = e < nf && !((dword[s] >> (list[e] & 31)) & 1u);
+                // a deletion after the search's epoch leaves the vertex live for it
+                if (e < nf && !live && a.ver.row_ver) live = ld_relaxed_u32(a.ver.del_ep + list[e]) > a.ver.epoch;
                 nlive += __popc(__ballot_sync(kFull, live));
                 cand[s] = live ? keys[e] : kPad;
                 if (cmpk(cand[s]) >= worst) cand[s] = kPad;

@@ -446,6 +446,65 @@ __device__ __forceinline__ uint32_t team_pair_key(int metric, const uint4 *ra, c
     return finish_key<DT>(metric, f, ia, 1.0f);
 }
 
+// ---------------------------------------------------------------- versions
+// Searches that overlap updates (the serving loop's update stream, Sec. 4.4,
+// with the consistency of Sec. 5.3).  Update number E (1, 2, ...) stamps
+// every existing graph row it rewrites with row_ver = E, after copying the
+// row's previous content into a shadow row, and every vertex it deletes with
+// del_ep = E before setting its bit.  A search of epoch e (the updates it
+// must see) reads a row stamped later than e from its shadow and treats a
+// vertex deleted later than e as live; vertices inserted later than e have
+// ids >= its n_used and are never named.  One shadow per row suffices: the
+// serving loop starts update E + 1 only after every search of an epoch
+// below E has finished.
+struct VerCtx {
+    const uint32_t *row_ver;     // [n_cap] update that last rewrote the row (0: none), or null: no versions
+    const int32_t *shadow_slot;  // [n_cap] shadow row holding the content before that update
+    const uint32_t *shadow;      // [slots][R]
+    const uint32_t *del_ep;      // [n_cap] update that deleted the vertex (where its bit is set)
+    uint32_t epoch;              // the search's epoch
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Graph row p (R = 32 S entries; lane l gets entries l, l + 32, ...) as a
+// search of epoch v.epoch sees it.  A row rewritten during the read is
+// detected by reading its stamp again after the row (the update stamps a row
+// before any kernel writes it), and is then read from its shadow.
+template <int S>
+__device__ __forceinline__ void versioned_row(const VerCtx &v, const uint32_t *graph, uint32_t p, int lane,
+                                              uint32_t (&nb)[S]) {
+    constexpr int R = 32 * S;
+    uint32_t ver = ld_acquire_u32(v.row_ver + p);
+    if (ver <= v.epoch) {
+#pragma unroll
+        for (int s = 0; s < S; s++) nb[s] = __ldcg(graph + (int64_t)p * R + s * 32 + lane);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        ver = ld_acquire_u32(v.row_ver + p);
+        if (ver <= v.epoch) return;
+    }
+    const int32_t slot = (int32_t)ld_relaxed_u32(reinterpret_cast<const uint32_t *>(v.shadow_slot) + p);
+#pragma unroll
+    for (int s = 0; s < S; s++) nb[s] = __ldcg(v.shadow + (int64_t)slot * R + s * 32 + lane);
+}
+
+// Deleted as of the search's epoch: its bit is set and its deletion was not
+// later than the epoch (a concurrent deletion is later: its del_ep is either
+// still unset, 0xFFFFFFFF, or already its own number, both above the epoch).
+__device__ __forceinline__ bool deleted_at(const VerCtx &v, const uint32_t *__restrict__ del, uint32_t id) {
+    if (!((__ldcg(del + (id >> 5)) >> (id & 31)) & 1u)) return false;
+    return ld_relaxed_u32(v.del_ep + id) <= v.epoch;
+}
+
 // Output value of a distance key: float, or int32 for a U8 store.
 __device__ __forceinline__ uint32_t key_to_out(uint32_t dk, int dtype, int metric) {
     if (dk == 0xFFFFFFFFu) return dtype == SVF_U8 ? 0x7FFFFFFFu : 0x7F800000u;  // INT32_MAX / +inf

@@ -68,6 +68,7 @@ struct SearchArgs {
     uint32_t stage_bytes;
     size_t warp_smem;
     int W;            // warps (parents per iteration) per query; 1: one warp per query
+    VerCtx ver;       // versioned reads (searches overlapping updates), or ver.row_ver == null
 };
 
 cudaError_t launch_search(SearchArgs a, int R, int L, cudaStream_t st);

@@ -74,6 +74,48 @@ __global__ void rev_merge_kernel(const RowDesc X, uint32_t *graph, int R, const 
     if (lane == 0) atomicAdd(status + kStRevTargets, 1ull);
 }
 
+// Copy row u into the next shadow row of the update, point u at it, then
+// stamp u with the update's number (release: the copy and the pointer are
+// visible before the stamp, and the stamp before any later kernel of the
+// update rewrites the row).
+__device__ __forceinline__ void stamp_row(const uint32_t *graph, int R, uint32_t u, const VerUpd &v,
+                                          unsigned long long *status) {
+    const unsigned long long k = atomicAdd(v.counter, 1ull);
+    if ((int64_t)k >= v.cap) {  // the caller sized the half for the update: a guard only
+        set_error(status, SVF_ECAPACITY, (long long)u);
+        return;
+    }
+    const int64_t slot = v.base + (int64_t)k;
+    for (int r = 0; r < R; r++) v.shadow[slot * R + r] = graph[(int64_t)u * R + r];
+    v.shadow_slot[u] = (int32_t)slot;
+    __threadfence();
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(v.row_ver + u), "r"(v.E) : "memory");
+}
+
+// One thread per request; the request at the head of its target's list
+// stamps the target (each target once).
+__global__ void stamp_targets_kernel(const uint32_t *graph, int R, const uint32_t *rows, int64_t nreq, int64_t tmax,
+                                     const int32_t *head, VerUpd v, unsigned long long *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nreq) return;
+    const uint32_t u = rows[i];
+    if (u == kEmpty || (int64_t)u >= tmax || head[u] != (int32_t)i) return;
+    stamp_row(graph, R, u, v, status);
+}
+
+__global__ void stamp_rows_kernel(const uint32_t *graph, int R, const uint32_t *vl, int64_t nv, VerUpd v,
+                                  unsigned long long *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv) stamp_row(graph, R, vl[i], v, status);
+}
+
+cudaError_t launch_stamp_rows(const uint32_t *graph, int R, const uint32_t *vl, int64_t nv, const VerUpd &ver,
+                              unsigned long long *status, cudaStream_t st) {
+    if (nv == 0) return cudaSuccess;
+    stamp_rows_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, st>>>(graph, R, vl, nv, ver, status);
+    return cudaGetLastError();
+}
+
 __global__ void rev_reset_kernel(const uint32_t *rows, int64_t nreq, int64_t tmax, int32_t *head) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nreq) return;
@@ -88,10 +130,13 @@ __global__ void iota_kernel(uint32_t *out, int64_t m, int64_t base) {
 
 cudaError_t launch_reverse_patch(const RowDesc &X, uint32_t *graph, int R, const uint32_t *del, int64_t n0, int64_t m,
                                  const uint32_t *rows, const uint32_t *dkeys, int64_t tmax, int32_t *head,
-                                 int32_t *next, unsigned long long *status, cudaStream_t st) {
+                                 int32_t *next, unsigned long long *status, cudaStream_t st, const VerUpd *ver) {
     const int64_t nreq = m * R;
     if (nreq == 0) return cudaSuccess;
     rev_link_kernel<<<(unsigned)((nreq + 255) / 256), 256, 0, st>>>(rows, nreq, tmax, head, next);
+    if (ver)
+        stamp_targets_kernel<<<(unsigned)((nreq + 255) / 256), 256, 0, st>>>(graph, R, rows, nreq, tmax, head, *ver,
+                                                                             status);
     const unsigned g = (unsigned)((nreq * 32 + 255) / 256);
     if (X.dtype == SVF_U8)
         rev_merge_kernel<SVF_U8><<<g, 256, 0, st>>>(X, graph, R, del, n0, rows, dkeys, nreq, tmax, head, next, status);
@@ -116,10 +161,15 @@ __global__ void del_validate_kernel(const uint32_t *ids, int64_t m, int64_t n_us
 }
 
 __global__ void del_mark_kernel(const uint32_t *ids, int64_t m, uint32_t *del, unsigned long long *status,
-                                long long *out_newly) {
+                                long long *out_newly, uint32_t *del_ep, uint32_t E) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m || status[kStScratch0] != 0ull) return;
     const uint32_t id = ids[i], bit = 1u << (id & 31);
+    if (del_ep) {
+        // the deletion's number first (a vertex already deleted keeps its own)
+        atomicMin(del_ep + id, E);
+        __threadfence();
+    }
     const uint32_t old = atomicOr(del + (id >> 5), bit);
     if (!(old & bit)) {
         atomicAdd(status + kStNewlyDeleted, 1ull);
@@ -268,11 +318,11 @@ __global__ void del_finalize_kernel(uint32_t *graph, int R, const uint32_t *del,
 }
 
 cudaError_t launch_delete_mark(const uint32_t *ids, int64_t m, int64_t n_used, uint32_t *del,
-                               unsigned long long *status, cudaStream_t st) {
+                               unsigned long long *status, cudaStream_t st, const VerUpd *ver) {
     if (m == 0) return cudaSuccess;
     const unsigned g = (unsigned)((m + 255) / 256);
     del_validate_kernel<<<g, 256, 0, st>>>(ids, m, n_used, status);
-    del_mark_kernel<<<g, 256, 0, st>>>(ids, m, del, status, nullptr);
+    del_mark_kernel<<<g, 256, 0, st>>>(ids, m, del, status, nullptr, ver ? ver->del_ep : nullptr, ver ? ver->E : 0u);
     return cudaGetLastError();
 }
 

@@ -286,11 +286,27 @@ class Server:
     """Continuous-batching request loop (svf_serve_*): submit searches,
     inserts and deletes; poll completions with host timestamps."""
 
-    def __init__(self, ix: Index, max_inflight: int = 8, n_streams: int = 4, maintain_every: int = 64):
+    CONSISTENCY = {"barrier": 0, "read-after-write": 1, "snapshot": 2}
+
+    def __init__(self, ix: Index, max_inflight: int = 8, n_streams: int = 4, maintain_every: int = 64,
+                 consistency: str = "barrier", shadow_rows: int | None = None):
+        """consistency: "barrier" (an update drains the searches and runs
+        alone), "read-after-write" (updates overlap earlier searches; a search
+        sees every update submitted before it) or "snapshot" (a search sees
+        the updates completed when it is admitted and never waits).  The two
+        versioned modes keep a device version buffer for up to `shadow_rows`
+        rewritten rows per update (default 2,048 inserted vectors' worth)."""
         self.ix = ix
         self.lib = L.load()
         h = C.c_void_p()
-        cfg = L.ServeCfg(max_inflight, n_streams, maintain_every, 0)
+        mode = self.CONSISTENCY[consistency]
+        self.versions = None
+        vb, rows = 0, 0
+        if mode:
+            rows = shadow_rows or 2048 * ix.R
+            vb = int(self.lib.svf_serve_version_bytes(ix._h, rows))
+            self.versions = torch.empty(vb, dtype=torch.uint8, device=ix.device)
+        cfg = L.ServeCfg(max_inflight, n_streams, maintain_every, mode, _ptr(self.versions), vb, rows)
         with torch.cuda.device(ix.device):
             L.check(self.lib.svf_serve_start(ix._h, C.byref(cfg), C.byref(h)))
         self._s = h

@@ -177,24 +177,13 @@ def _trace(rng, n_req, n_start, X, n_base):
     return reqs
 
 
-@pytest.mark.parametrize("tiered", [False, True])
-def test_server_results_equal_alone(svf, tiered):
-    """Each search served in the mix equals the same search run alone on the
-    index state of its epoch; updates advance the epoch in submission order."""
-    n0, ncap = 8000, 12000
-    X, ix = built(svf, "u8", n0, ncap, R=32, max_batch=8000)
-    _, ref_ix = built(svf, "u8", n0, ncap, R=32, max_batch=8000)
-    if tiered:
-        ix.enable_tier(M=1500, theta0=0.5, promote_batch=256, qcap=4096)
-        ix.release_device_store()
-    rng = np.random.default_rng(731)
-    reqs = _trace(rng, 120, n0, X, n0)
-    srv = svf.Server(ix, max_inflight=6, n_streams=4, maintain_every=4)
-    cfg = svf.SearchConfig(k=10, L=64, T=32)
-    outs = {}
+def _serve_trace(svf, ix, X, n0, reqs, cfg, consistency, **kw):
+    """Submit the trace at once (so searches and updates overlap), drain, and
+    return the completions, the search outputs and the update inputs."""
+    srv = svf.Server(ix, max_inflight=6, n_streams=4, maintain_every=4, consistency=consistency, **kw)
+    outs, dev_inputs = {}, []
     deleted = set()
     n_used = n0
-    dev_inputs = []
     for tag, (op, a, b) in enumerate(reqs):
         if op == "search":
             Q = torch.from_numpy(synth.sample("u8", b, 10_000 + tag)).cuda()
@@ -217,27 +206,121 @@ def test_server_results_equal_alone(svf, tiered):
     comps = {c["tag"]: c for c in srv.poll(10000)}
     srv.stop()
     assert len(comps) == len(reqs) and all(c["status"] == 0 for c in comps.values())
-    # replay alone, in order
-    upd = {t: (k, v) for t, k, v in dev_inputs}
-    epoch = 0
+    return comps, outs, {t: (k, v) for t, k, v in dev_inputs}, n_used
+
+
+def _check_epochs(reqs, comps, consistency):
+    """Update E completes with epoch E (submission order).  A search's epoch
+    is every update submitted before it (barrier, read-after-write) or, in the
+    snapshot mode, at most that.  Returns {epoch: [search tags]}."""
+    by_epoch, submitted = {}, 0
     for tag, (op, a, b) in enumerate(reqs):
         c = comps[tag]
         assert c["t_done"] >= c["t_start"] > 0
         if op == "search":
-            assert c["epoch"] == epoch
-            Q, oi, od = outs[tag]
-            ri, rd = ref_ix.search(Q, cfg)
-            assert torch.equal(ri, oi) and torch.equal(rd, od), f"request {tag}"
-        else:
-            kind, v = upd[tag]
-            if kind == "insert":
-                ref_ix.insert(v, L_ins=64, T_ins=32)
+            if consistency == "snapshot":
+                assert c["epoch"] <= submitted
             else:
-                ref_ix.delete(v)
-            epoch += 1
-            assert c["epoch"] == epoch
+                assert c["epoch"] == submitted, (tag, c["epoch"], submitted)
+            by_epoch.setdefault(c["epoch"], []).append(tag)
+        else:
+            submitted += 1
+            assert c["epoch"] == submitted
+    return by_epoch
+
+
+def _overlaps(reqs, comps):
+    """Searches of an older epoch whose host interval overlapped an update."""
+    n = 0
+    ups = [comps[t] for t, r in enumerate(reqs) if r[0] != "search"]
+    for t, r in enumerate(reqs):
+        if r[0] != "search":
+            continue
+        c = comps[t]
+        n += any(u["epoch"] > c["epoch"] and u["t_start"] < c["t_done"] and c["t_start"] < u["t_done"] for u in ups)
+    return n
+
+
+@pytest.mark.parametrize("consistency,tiered", [("barrier", False), ("barrier", True), ("read-after-write", False),
+                                                 ("snapshot", False), ("snapshot", True)])
+def test_server_results_equal_alone(svf, consistency, tiered):
+    """Each search served in the mix equals the same search run alone on the
+    index state of its epoch; updates advance the epoch in submission order.
+    In the versioned modes updates overlap searches of older epochs, which
+    read the rows the update rewrites from their shadows."""
+    n0, ncap = 8000, 12000
+    X, ix = built(svf, "u8", n0, ncap, R=32, max_batch=8000)
+    _, ref_ix = built(svf, "u8", n0, ncap, R=32, max_batch=8000)
+    if tiered:
+        ix.enable_tier(M=1500, theta0=0.5, promote_batch=256, qcap=4096)
+        ix.release_device_store()
+    rng = np.random.default_rng(731)
+    reqs = _trace(rng, 120, n0, X, n0)
+    cfg = svf.SearchConfig(k=10, L=64, T=32)
+    comps, outs, upd, n_used = _serve_trace(svf, ix, X, n0, reqs, cfg, consistency)
+    by_epoch = _check_epochs(reqs, comps, consistency)
+    # replay alone, in order, each search at its epoch
+    epoch = 0
+    for tag, (op, a, b) in enumerate(reqs + [("end", 0, 0)]):
+        if op == "search":
+            continue
+        for t in by_epoch.pop(epoch, []):
+            Q, oi, od = outs[t]
+            ri, rd = ref_ix.search(Q, cfg)
+            assert torch.equal(ri, oi) and torch.equal(rd, od), f"request {t} at epoch {epoch}"
+        if op == "end":
+            break
+        kind, v = upd[tag]
+        if kind == "insert":
+            ref_ix.insert(v, L_ins=64, T_ins=32)
+        else:
+            ref_ix.delete(v)
+        epoch += 1
+    assert not by_epoch
     torch.cuda.synchronize()
     assert torch.equal(ix.graph[:n_used], ref_ix.graph[:n_used])
+    if consistency != "barrier":
+        assert _overlaps(reqs, comps) > 0, "no update overlapped an older search"
+
+
+@pytest.mark.parametrize("consistency", ["read-after-write", "snapshot"])
+def test_served_searches_match_oracle_at_their_epochs(svf, orc, consistency):
+    """Oracle replay of the served stream: the FP64 oracle applies the same
+    inserts and deletes in submission order (Sec. 5.1, 5.2) and searches
+    every served batch on the index state of its epoch; uint8 data, so ids
+    and distances agree bit for bit."""
+    n0, ncap = 6000, 9000
+    X, ix = built(svf, "u8", n0, ncap, R=32, max_batch=6000)
+    g = np.full((ncap, 32), orc.EMPTY, dtype=np.uint32)
+    g[:n0] = P.as_u32(ix.graph[:n0].cpu().numpy())
+    st = orc.Store.from_vectors(X, "l2")
+    bits = orc.bitset(ncap)
+    rng = np.random.default_rng(741)
+    reqs = _trace(rng, 100, n0, X, n0)
+    cfg = svf.SearchConfig(k=10, L=64, T=32)
+    comps, outs, upd, n_used = _serve_trace(svf, ix, X, n0, reqs, cfg, consistency)
+    by_epoch = _check_epochs(reqs, comps, consistency)
+    seed = ix.params.seed
+    n, epoch, checked = n0, 0, 0
+    for tag, (op, a, b) in enumerate(reqs + [("end", 0, 0)]):
+        if op == "search":
+            continue
+        for t in by_epoch.pop(epoch, []):
+            Q, oi, od = outs[t]
+            o = orc.search(st, n, g, bits, Q.cpu().numpy(), 10, 64, 32, seed)
+            P.check_exact(oi.cpu().numpy(), od.cpu().numpy(), o)
+            checked += 1
+        if op == "end":
+            break
+        kind, v = upd[tag]
+        if kind == "insert":
+            orc.insert(st, n, b, g, bits, 64, 32, seed)
+            n += b
+        else:
+            orc.delete(st, n, g, bits, v.cpu().numpy().view(np.uint32))
+        epoch += 1
+    assert not by_epoch and checked > 50
+    np.testing.assert_array_equal(P.as_u32(ix.graph[:n].cpu().numpy()), g[:n])
 
 
 def test_tiered_lowp_rerank_equals_device(svf):
