@@ -65,8 +65,14 @@ def parse():
     ap.add_argument("--serve-rates", default="25,50,100,200")
     ap.add_argument("--serve-form", default="fp32", choices=["fp32", "fp8"],
                     help="serving traversal: fp32 rows through the tier, or a resident fp8 copy + exact re-rank")
+    ap.add_argument("--cache-ratios", default="0.1",
+                    help="cache sizes (fractions of n) of the placement ablation on a moving hot set (empty: skip)")
+    ap.add_argument("--cache-policies", default="wavp,lru,lrfu",
+                    help="placement policies of that ablation (wavp,clock,lfu,static,lru,lrfu)")
+    ap.add_argument("--cache-seconds", type=float, default=6.0)
+    ap.add_argument("--cache-rate", type=float, default=50.0)
     ap.add_argument("--serve-policies", default="",
-                    help="comma list of extra cache placement policies (clock,lfu,static) run on the same serving "
+                    help="comma list of extra cache placement policies (clock,lfu,static,lru,lrfu) run on the same serving "
                          "stream after WAVP, for the ablation")
     ap.add_argument("--serve-window", default="",
                     help="W,speed: queries from a sliding window of W components moving `speed` components/s "
@@ -719,7 +725,10 @@ def main():
     policies = [p for p in a.serve_policies.split(",") if p]
     # capacity for the inserts of every serving stream: the main one, the
     # one-warp-per-query rerun and the placement ablation
-    ix = build_index(svf, torch, X, log_t, streams=5 + len(policies))
+    ratios = [float(x) for x in a.cache_ratios.split(",") if x]
+    cpols = [p for p in a.cache_policies.split(",") if p]
+    # insert headroom: 300K rows per serving stream, 100K per ablation stream
+    ix = build_index(svf, torch, X, log_t, streams=5 + len(policies) + (len(ratios) * len(cpols) + 2) // 3)
     Xd = ix.vectors()[:a.n]
     Qe = torch.from_numpy(Qe_np).cuda()
     gt = exact_knn(svf, Xd, Qe, K, "ip")
@@ -906,7 +915,11 @@ def main():
         if win_arg:
             win_arg = (int(win_arg[0]), win_arg[1])
         sopt = dict(maintain_every=a.serve_maintain_every, window=win_arg)
-        ix.enable_tier(**tier)
+        # the buffers hold the largest cache any run below uses; runs reset it smaller
+        m_alloc = int(a.n * max([a.serve_cache_frac] + ratios))
+        ix.enable_tier(**dict(tier, M=m_alloc))
+        if m_alloc != tier["M"]:
+            ix.reset_tier(**tier)
         X_ins = synth.sample_chunked("unit96", 200_000, 305)
         if a.serve_trav == "fp32":
             fp = best.get("fp32", {"L": 64, "T": 96})
@@ -966,6 +979,30 @@ def main():
                 r["policy"] = p
                 out["serving_policies"][p] = r
                 log_t("serving", p, json.dumps(r))
+        if ratios:
+            # placement ablation (Sec. 6.3) on a moving hot set: queries from a
+            # window of 64 components advancing 4 per second, every traversal
+            # row (fp32) read through the tier, maintenance every 16 search
+            # batches; each policy at each cache size, from a cold start
+            fp = best.get("fp32", {"L": 64, "T": 96})
+            c32 = svf.SearchConfig(k=K, L=fp["L"], T=fp["T"])
+            wopt = dict(maintain_every=16, window=(64, 4.0))
+            sweep_out = {"workload": (f"unit96-10M tiered, fp32 traversal through the tier (L={fp['L']}, T={fp['T']}), "
+                                      f"queries from a window of 64 components moving 4/s, {a.cache_rate:g} req/s "
+                                      f"for {a.cache_seconds:g} s, 90:9:1 mix, maintenance every 16 search batches"),
+                         "by_ratio": {}}
+            for r in ratios:
+                row = {}
+                for p in cpols:
+                    ix.reset_tier(**dict(tier, M=int(a.n * r), policy=p))
+                    res = serve_stream(svf, torch, ix, "unit96", X_ins, a.cache_rate, a.cache_seconds, 1.0, 309, c32,
+                                       **wopt)
+                    row[p] = {"cache_hit_rate": res["cache_hit_rate"], "qps": res["qps"], "promoted": res["promoted"],
+                              "search_p50_ms": res["latency_ms"]["search"]["p50"],
+                              "search_p99_ms": res["latency_ms"]["search"]["p99"]}
+                    log_t("cache ablation", r, p, json.dumps(row[p]))
+                sweep_out["by_ratio"][f"{r:g}"] = row
+            out["cache_ablation"] = sweep_out
     # deletes (1% of the index, uniformly drawn live ids) with localized repair
     dels = torch.from_numpy(synth.pick_live_ids(a.n, gone, a.n // 100, 304).view(np.int32)).cuda()
     torch.cuda.synchronize()

@@ -128,7 +128,10 @@ typedef struct {
  *             iterations, so a query expands up to W*T parents.  W > 1 does
  *             not combine with mlp / trace_feat / trace_meta (SVF_EINVAL).
  *             Meant for small batches, where one warp per query leaves most
- *             of the GPU idle. */
+ *             of the GPU idle.
+ *   wpq       warps per query when W = 2: 0 as above (a CTA of W warps), or
+ *             1: one warp expands both parents of an iteration (same results;
+ *             twice the rows in flight per warp, for full batches). */
 typedef struct {
     int32_t k;
     int32_t L;
@@ -146,6 +149,8 @@ typedef struct {
     uint64_t *pool_out;
     int32_t t_every;
     int32_t W;
+    int32_t wpq;
+    int32_t reserved0;
 } svf_search_params;
 
 /* Running counters (since svf_create or svf_stats_reset). */
@@ -287,12 +292,28 @@ int svf_knn(const void *X, int64_t n, int32_t d, int32_t dtype, int32_t metric, 
  * inserted rows, so BF16/FP8 traversal reads no host memory and only the
  * exact re-rank goes through the tier. */
 /* Placement policies (svf_tier_params.policy).  WAVP is the paper's
- * (Alg. 2, Eq. 2); the others are ablations of it on the same machinery:
+ * (Alg. 2, Eq. 2); the others are the baselines of its Sec. 6.3 on the same
+ * machinery (a maintenance round promotes up to promote_batch queued rows
+ * into victims chosen among the sweep * promote_batch slots the clock
+ * passes, an empty slot first):
  * CLOCK admits every missed row in miss order and evicts the first
  * unreferenced slots the clock meets (second chance: recency only); LFU
  * admits and evicts by F_recent alone (beta ignored, theta fixed at theta0);
- * STATIC keeps the cold-start cache of the highest in-degree rows. */
-enum svf_tier_policy { SVF_TIER_WAVP = 0, SVF_TIER_CLOCK = 1, SVF_TIER_LFU = 2, SVF_TIER_STATIC = 3 };
+ * STATIC keeps the cold-start cache of the highest in-degree rows; LRU
+ * admits every missed row in miss order and evicts the slots whose last hit
+ * is oldest (hits are stamped with a counter of the calls that read the
+ * tier); LRFU admits every missed row and evicts the slots of lowest
+ * combined recency-frequency C = sum over hits of 2^(-lambda * age), age in
+ * maintenance rounds (C <- C * 2^-lambda + hits of the round; a promoted row
+ * starts at 1 for the miss that admitted it). */
+enum svf_tier_policy {
+    SVF_TIER_WAVP = 0,
+    SVF_TIER_CLOCK = 1,
+    SVF_TIER_LFU = 2,
+    SVF_TIER_STATIC = 3,
+    SVF_TIER_LRU = 4,
+    SVF_TIER_LRFU = 5
+};
 
 typedef struct {
     int64_t M;              /* cache slots */
@@ -303,18 +324,20 @@ typedef struct {
     float theta0;           /* initial promotion threshold */
     uint64_t decay_every;   /* halve F_recent after this many misses */
     int32_t policy;         /* svf_tier_policy */
-    int32_t reserved0;
+    float lrfu_lambda;      /* LRFU decay per maintenance round (0: 0.5) */
 } svf_tier_params;
 
 typedef struct {
     size_t cache, map, owner, ref, freq, ein, queue, scratch; /* device bytes */
     size_t host;                                              /* pinned host bytes */
+    size_t slot_stat;                                         /* device bytes: per-slot LRU / LRFU state */
 } svf_tier_sizes;
 
 typedef struct {
     void *cache; int32_t *map; int32_t *owner; uint8_t *ref; uint32_t *freq; uint32_t *ein; uint32_t *queue;
     void *scratch;
     void *host;  /* pinned (cudaHostAlloc / page-locked) host memory for n_cap rows */
+    void *slot_stat;
 } svf_tier_buffers;
 
 int svf_tier_buffer_sizes(const svf_params *p, const svf_tier_params *tp, svf_tier_sizes *out);
@@ -325,10 +348,11 @@ int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream);
 /* Current promotion threshold. */
 float svf_tier_theta(svf_index *h);
 /* Re-initialise a tiered store with new parameters (policy, weights,
- * threshold; M and the buffers stay): miss counts, queue and reference bits
- * are cleared, E_in is recomputed from the current graph and the cache is
- * warmed again with the highest in-degree rows, read from the host store.
- * Must not run while a search or update on the index is in flight. */
+ * threshold, and a cache of M slots, at most the M it was enabled with; the
+ * buffers stay): miss counts, queue and reference bits are cleared, E_in is
+ * recomputed from the current graph and the cache is warmed again with the
+ * highest in-degree rows, read from the host store.  Must not run while a
+ * search or update on the index is in flight. */
 int svf_tier_reset(svf_index *h, const svf_tier_params *tp, void *stream);
 
 /* ---- continuous-batching request loop (Sec. 4.4 real-time coordination,

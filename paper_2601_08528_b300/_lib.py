@@ -52,7 +52,7 @@ class SearchParams(C.Structure):
                 ("rerank", C.c_int32), ("t_min", C.c_int32), ("mlp", C.c_void_p), ("z_tau", C.c_float),
                 ("hash_log2", C.c_int32), ("qkeys", C.c_void_p), ("seed", C.c_uint64), ("trace_feat", C.c_void_p),
                 ("trace_meta", C.c_void_p), ("pool_out", C.c_void_p), ("t_every", C.c_int32),
-                ("W", C.c_int32)]
+                ("W", C.c_int32), ("wpq", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class Counters(C.Structure):
@@ -65,18 +65,20 @@ class Counters(C.Structure):
 class TierParams(C.Structure):
     _fields_ = [("M", C.c_int64), ("qcap", C.c_uint32), ("promote_batch", C.c_int32), ("sweep", C.c_int32),
                 ("alpha", C.c_float), ("beta", C.c_float), ("theta0", C.c_float), ("decay_every", C.c_uint64),
-                ("policy", C.c_int32), ("reserved0", C.c_int32)]
+                ("policy", C.c_int32), ("lrfu_lambda", C.c_float)]
 
 
-TIER_POLICIES = {"wavp": 0, "clock": 1, "lfu": 2, "static": 3}
+TIER_POLICIES = {"wavp": 0, "clock": 1, "lfu": 2, "static": 3, "lru": 4, "lrfu": 5}
 
 
 class TierSizes(C.Structure):
-    _fields_ = [(f, C.c_size_t) for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch", "host")]
+    _fields_ = [(f, C.c_size_t) for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch", "host",
+                                          "slot_stat")]
 
 
 class TierBuffers(C.Structure):
-    _fields_ = [(f, C.c_void_p) for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch", "host")]
+    _fields_ = [(f, C.c_void_p) for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch", "host",
+                                          "slot_stat")]
 
 
 OP_SEARCH, OP_INSERT, OP_DELETE = 0, 1, 2

@@ -231,10 +231,15 @@ static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search
     a.k = sp->k;
     a.T = sp->T;
     a.W = sp->W > 1 ? sp->W : 1;
-    // up to W*R new ids per iteration (W parents); with W > 1 the default
-    // table holds about four iterations' ids, so resets stay as rare as with
-    // one parent per iteration
-    a.hash_bits = hash_bits_for(sp->L, a.W * h->p.R, sp->hash_log2, a.W > 1 ? 4 : 1);
+    a.wp = 1;
+    if (a.W == 2 && sp->wpq == 1) {  // one warp, two parents per iteration
+        a.W = 1;
+        a.wp = 2;
+    }
+    // up to W*R new ids per iteration (W parents); with W > 1 warps the
+    // default table holds about four iterations' ids, so resets stay as rare
+    // as with one parent per iteration
+    a.hash_bits = hash_bits_for(sp->L, a.W * a.wp * h->p.R, sp->hash_log2, a.W > 1 ? 4 : 1);
     a.rerank = sp->rerank;
     a.out_dtype = h->p.dtype;
     a.out_ids = out_ids;
@@ -272,6 +277,7 @@ static int check_search(svf_index *h, const svf_search_params *sp, RowDesc *trav
         return fail(SVF_EINVAL, "W must be 0, 1, 2, 4 or 8");
     if (sp->W > 1 && (sp->mlp || sp->trace_feat || sp->trace_meta))
         return fail(SVF_EINVAL, "the stop network and traces run with one warp per query (W <= 1)");
+    if (sp->wpq != 0 && !(sp->wpq == 1 && sp->W == 2)) return fail(SVF_EINVAL, "wpq = 1 needs W = 2");
     *trav_out = trav;
     return SVF_OK;
 }

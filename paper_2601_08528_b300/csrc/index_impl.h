@@ -70,6 +70,10 @@ struct Tier {
     int64_t clock = 0;
     uint64_t last_hits = 0, last_misses = 0, misses_at_decay = 0, rounds = 0;
     double last_rate = 0.0, last_meanf = 0.0;
+    int64_t M_alloc = 0;           // slots the buffers hold (M <= M_alloc after a reset)
+    uint32_t *stat = nullptr;      // [M_alloc][2] LRU / LRFU state
+    float lambda = 0.5f;           // LRFU decay per round
+    mutable uint32_t tick = 0;     // LRU stamp, advanced per call that reads the tier
 };
 
 // Global consolidation in progress (consolidate.cu): a snapshot of the
@@ -153,9 +157,15 @@ struct svf_index {
         // F_recent over the fixed theta (LFU), nothing (STATIC)
         t.alpha = tier.policy == SVF_TIER_WAVP ? tier.alpha : 1.f;
         t.beta = tier.policy == SVF_TIER_WAVP ? tier.beta : 0.f;
-        t.theta = tier.policy == SVF_TIER_CLOCK    ? -1.f
-                  : tier.policy == SVF_TIER_STATIC ? INFINITY
-                                                   : tier.theta;
+        const bool lr = tier.policy == SVF_TIER_LRU || tier.policy == SVF_TIER_LRFU;
+        t.theta = tier.policy == SVF_TIER_CLOCK || lr ? -1.f
+                  : tier.policy == SVF_TIER_STATIC    ? INFINITY
+                                                      : tier.theta;
+        if (lr) {
+            t.stat = tier.stat;
+            t.lru = tier.policy == SVF_TIER_LRU;
+            t.tick = ++tier.tick;
+        }
         return t;
     }
 };

@@ -592,8 +592,23 @@ struct TierCtx {
     unsigned long long *qcount;
     uint32_t qcap;
     float alpha, beta, theta;
+    uint32_t *stat;        // per slot, 2 words: LRU [last hit stamp, -], LRFU [hits this round, C (f32)]; or null
+    uint32_t tick;         // stamp of this call's hits (LRU)
+    int lru;               // 1: LRU stamps, 0: LRFU counts (when stat is set)
 };
 constexpr uint32_t kQueuedBit = 0x80000000u;
+
+// A cache hit on slot s: the reference bit (clock policies) and the LRU /
+// LRFU recency state.
+__device__ __forceinline__ void tier_hit(const TierCtx &T, int32_t s) {
+    T.ref[s] = 1;
+    if (T.stat) {
+        if (T.lru)
+            T.stat[2 * (int64_t)s] = T.tick;
+        else
+            atomicAdd(T.stat + 2 * (int64_t)s, 1u);
+    }
+}
 
 __device__ __forceinline__ void tier_miss(const TierCtx &T, uint32_t id) {
     const uint32_t old = atomicAdd(T.freq + id, 1u);
@@ -678,7 +693,7 @@ __device__ __forceinline__ bool staged_dist(Stage &S, const RowDesc &R, const ui
                 const int32_t slot = __ldg(R.map + id);
                 if (slot >= 0) {
                     bulk_g2s(S.buf + (size_t)j * cb, R.base + (int64_t)slot * R.pitch, cb, S.mbar);
-                    tier->ref[slot] = 1;
+                    tier_hit(*tier, slot);
                 } else {
                     mmask |= 1u << t;
                     tier_miss(*tier, id);

@@ -115,6 +115,54 @@ __global__ void victim_kernel(const int32_t *owner, uint8_t *ref, const uint32_t
     atomicAdd(nvalid, 1ull);
 }
 
+// LRU / LRFU victims: every slot of the window, ordered by the last-hit stamp
+// (LRU) or by C (LRFU), ascending; an empty slot first; ties by slot.
+__global__ void victim_recency_kernel(const int32_t *owner, const uint32_t *stat, int lru, int64_t M, int64_t hand,
+                                      int64_t W, int64_t npow, uint64_t *keys, unsigned long long *nvalid) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npow) return;
+    if (i >= W) {
+        keys[i] = kPad;
+        return;
+    }
+    const int64_t s = (hand + i) % M;
+    uint32_t k;
+    if (owner[s] < 0)
+        k = 0u;
+    else if (lru)
+        k = stat[2 * s] + 1u;  // stamps are below 2^32 - 1
+    else
+        k = fkey(__uint_as_float(stat[2 * s + 1]));  // C >= 0 sorts after the empty key 0
+    keys[i] = make_key(k, (uint32_t)s);
+    atomicAdd(nvalid, 1ull);
+}
+
+// LRFU: fold the round's hits into C (C <- C * 2^-lambda + hits) for every slot.
+__global__ void lrfu_fold_kernel(uint32_t *stat, int64_t M, float decay) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const float c = __uint_as_float(stat[2 * s + 1]) * decay + (float)stat[2 * s];
+    stat[2 * s + 1] = __float_as_uint(c);
+    stat[2 * s] = 0u;
+}
+
+// Recency state of the slots just filled: LRU stamp = this round's tick,
+// LRFU C = 1 (the miss that admitted the row).
+__global__ void promoted_stat_kernel(const uint64_t *promo, const uint64_t *victims, int64_t nb, uint32_t *stat,
+                                     int lru, uint32_t tick) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const uint64_t pk = promo[i], vk = victims[i];
+    if (key_is_pad(pk) || key_is_pad(vk)) return;
+    const uint32_t s = (uint32_t)vk;
+    if (lru) {
+        stat[2 * (int64_t)s] = tick;
+    } else {
+        stat[2 * (int64_t)s] = 0u;
+        stat[2 * (int64_t)s + 1] = __float_as_uint(1.f);
+    }
+}
+
 // Single-CTA ascending bitonic sort of npow (power of two, <= 16384) keys.
 __global__ void __launch_bounds__(1024) sort_kernel(uint64_t *keys, int npow) {
     extern __shared__ uint64_t sk[];
@@ -200,12 +248,16 @@ int tier_init(svf_index *h, const svf_tier_params *tp, const uint8_t *src, cudaS
     T.sweep = tp->sweep;
     T.decay_every = tp->decay_every ? tp->decay_every : (1ull << 16);
     T.policy = tp->policy;
+    T.M = tp->M;
+    T.lambda = tp->lrfu_lambda > 0.f ? tp->lrfu_lambda : 0.5f;
+    T.tick = 0;
     T.clock = 0;
     T.rounds = 0;
     T.last_rate = T.last_meanf = 0.0;
     CUDA_TRY(cudaMemsetAsync(T.map, 0xFF, (size_t)h->p.n_cap * 4, st));
     CUDA_TRY(cudaMemsetAsync(T.owner, 0xFF, (size_t)T.M * 4, st));
     CUDA_TRY(cudaMemsetAsync(T.ref, 0, (size_t)T.M, st));
+    CUDA_TRY(cudaMemsetAsync(T.stat, 0, (size_t)T.M * 8, st));
     CUDA_TRY(cudaMemsetAsync(T.freq, 0, (size_t)h->p.n_cap * 4, st));
     CUDA_TRY(cudaMemsetAsync(T.ein, 0, (size_t)h->p.n_cap * 4, st));
     CUDA_TRY(cudaMemsetAsync(h->status() + kStQCount, 0, 8, st));
@@ -253,7 +305,8 @@ int svf_tier_buffer_sizes(const svf_params *p, const svf_tier_params *tp, svf_ti
     if (tp->promote_batch < 1 || tp->promote_batch > 2048) return fail(SVF_EINVAL, "promote_batch in [1, 2048]");
     if (tp->sweep < 1 || (int64_t)tp->sweep * tp->promote_batch > kMaxSweep)
         return fail(SVF_EINVAL, "sweep * promote_batch must be <= 8192");
-    if (tp->policy < SVF_TIER_WAVP || tp->policy > SVF_TIER_STATIC) return fail(SVF_EINVAL, "unknown tier policy");
+    if (tp->policy < SVF_TIER_WAVP || tp->policy > SVF_TIER_LRFU) return fail(SVF_EINVAL, "unknown tier policy");
+    if (!(tp->lrfu_lambda >= 0.f)) return fail(SVF_EINVAL, "lrfu_lambda must be >= 0");
     const int64_t pitch = (int64_t)p->d * esize_of(p->dtype);
     out->cache = align256((size_t)tp->M * pitch);
     out->map = align256((size_t)p->n_cap * 4);
@@ -264,6 +317,7 @@ int svf_tier_buffer_sizes(const svf_params *p, const svf_tier_params *tp, svf_ti
     out->queue = align256((size_t)tp->qcap * 4);
     out->scratch = align256((size_t)(kMaxQueue + kMaxSweep) * 8 + kHistBins * 8 + 64);
     out->host = (size_t)p->n_cap * pitch;
+    out->slot_stat = align256((size_t)tp->M * 8);
     return SVF_OK;
 }
 
@@ -274,7 +328,7 @@ int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buff
     int rc = svf_tier_buffer_sizes(&h->p, tp, &sz);
     if (rc) return rc;
     if (!tb->cache || !tb->map || !tb->owner || !tb->ref || !tb->freq || !tb->ein || !tb->queue || !tb->scratch ||
-        !tb->host)
+        !tb->host || !tb->slot_stat)
         return fail(SVF_EINVAL, "a tier buffer is null");
     cudaStream_t st = (cudaStream_t)stream;
     h->last = st;
@@ -291,6 +345,8 @@ int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buff
     T.ein = tb->ein;
     T.queue = tb->queue;
     T.scratch = reinterpret_cast<uint64_t *>(tb->scratch);
+    T.stat = reinterpret_cast<uint32_t *>(tb->slot_stat);
+    T.M_alloc = tp->M;
     // host copy of the rows, then the tables and the warm cache
     if (n) CUDA_TRY(cudaMemcpyAsync(T.host, h->b.vecs, (size_t)n * pitch, cudaMemcpyDeviceToHost, st));
     rc = tier_init(h, tp, reinterpret_cast<const uint8_t *>(h->b.vecs), st);
@@ -302,7 +358,7 @@ int svf_tier_enable(svf_index *h, const svf_tier_params *tp, const svf_tier_buff
 int svf_tier_reset(svf_index *h, const svf_tier_params *tp, void *stream) {
     if (!h || !tp) return fail(SVF_EINVAL, "null arguments");
     if (!h->tier.on) return fail(SVF_EINVAL, "the store is not tiered");
-    if (tp->M != h->tier.M) return fail(SVF_EINVAL, "reset keeps the cache size M");
+    if (tp->M > h->tier.M_alloc) return fail(SVF_EINVAL, "reset: M exceeds the slots the buffers hold");
     svf_tier_sizes sz;
     const int rc = svf_tier_buffer_sizes(&h->p, tp, &sz);
     if (rc) return rc;
@@ -322,7 +378,12 @@ int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream) {
     CUDA_TRY(cudaMemcpy(s, h->status(), sizeof s, cudaMemcpyDeviceToHost));
     // STATIC keeps its cold-start cache (nothing is ever queued)
     const int64_t c = T.policy == SVF_TIER_STATIC ? 0 : (int64_t)std::min<unsigned long long>(s[kStQCount], T.qcap);
-    const int by_order = T.policy == SVF_TIER_CLOCK;
+    const bool lr = T.policy == SVF_TIER_LRU || T.policy == SVF_TIER_LRFU;
+    const int by_order = T.policy == SVF_TIER_CLOCK || lr;
+    if (T.policy == SVF_TIER_LRFU && T.M > 0) {
+        lrfu_fold_kernel<<<grid_for(T.M, 256), 256, 0, st>>>(T.stat, T.M, exp2f(-T.lambda));
+        CUDA_TRY(cudaGetLastError());
+    }
     const float wa = T.policy == SVF_TIER_WAVP ? T.alpha : 1.f, wb = T.policy == SVF_TIER_WAVP ? T.beta : 0.f;
     const unsigned long long prom0 = s[kStPromoted];
     float meanf = 0.f;
@@ -344,17 +405,25 @@ int svf_tier_maintain(svf_index *h, int64_t *out_promoted, void *stream) {
         // it comes round again (all reference bits are clear by then)
         unsigned long long *nvalid = reinterpret_cast<unsigned long long *>(fsum + 2);
         CUDA_TRY(cudaMemsetAsync(nvalid, 0, 8, st));
-        victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw, wa, wb,
-                                                          by_order, vk, nvalid);
-        unsigned long long nv = 0;
-        CUDA_TRY(cudaMemcpyAsync(&nv, nvalid, 8, cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-        if ((int64_t)nv < B)
-            victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw,
-                                                              wa, wb, by_order, vk, nvalid);
+        if (lr) {
+            victim_recency_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.stat, T.policy == SVF_TIER_LRU, T.M,
+                                                                      T.clock, W, nw, vk, nvalid);
+        } else {
+            victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw, wa,
+                                                              wb, by_order, vk, nvalid);
+            unsigned long long nv = 0;
+            CUDA_TRY(cudaMemcpyAsync(&nv, nvalid, 8, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if ((int64_t)nv < B)
+                victim_kernel<<<grid_for(nw, 256), 256, 0, st>>>(T.owner, T.ref, T.freq, T.ein, T.M, T.clock, W, nw,
+                                                                  wa, wb, by_order, vk, nvalid);
+        }
         sort_kernel<<<1, 1024, nw * 8, st>>>(vk, (int)nw);
         apply_kernel<<<grid_for(B * 32, 256), 256, 0, st>>>(pk, vk, B, T.map, T.owner, T.ref, T.host, T.cache, pitch,
                                                              h->status());
+        if (lr)
+            promoted_stat_kernel<<<grid_for(B, 256), 256, 0, st>>>(pk, vk, B, T.stat, T.policy == SVF_TIER_LRU,
+                                                                    T.tick);
         unqueue_kernel<<<grid_for(c, 256), 256, 0, st>>>(T.queue, c, T.freq);
         CUDA_TRY(cudaMemsetAsync(h->status() + kStQCount, 0, 8, st));
         CUDA_TRY(cudaGetLastError());

@@ -38,6 +38,7 @@ class SearchConfig:
     t_min: int = 4
     t_every: int = 1
     W: int = 1     # parents per iteration = warps per query (1, 2, 4, 8)
+    wpq: int = 0   # 1: with W = 2, one warp expands both parents (full batches)
 
 
 class Index:
@@ -143,7 +144,7 @@ class Index:
         z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
         sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
                             cfg.hash_log2, _ptr(qkeys), cfg.seed, _ptr(trace_feat), _ptr(trace_meta), _ptr(pool_out),
-                            cfg.t_every, cfg.W)
+                            cfg.t_every, cfg.W, cfg.wpq, 0)
         L.check(L.load().svf_search(self._h, _ptr(Q), nq, C.byref(sp), _ptr(out_ids), _ptr(out_dist),
                                     _stream(stream)))
         return out_ids, out_dist
@@ -200,29 +201,33 @@ class Index:
 
     # ------------------------------------------------------------ tiered store
     def enable_tier(self, M: int, qcap: int = 16384, promote_batch: int = 2048, sweep: int = 4, alpha: float = 0.6,
-                    beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp") -> None:
+                    beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp",
+                    lrfu_lambda: float = 0.5) -> None:
         """Move the primary rows to pinned host memory behind a device cache of
         M rows with workload-aware placement (see svf_tier_enable; policy:
-        wavp, clock, lfu or static)."""
+        wavp, clock, lfu, static, lru or lrfu)."""
         lib = L.load()
-        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every, L.TIER_POLICIES[policy], 0)
+        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every, L.TIER_POLICIES[policy],
+                          lrfu_lambda)
         sz = L.TierSizes()
         L.check(lib.svf_tier_buffer_sizes(C.byref(self.params), C.byref(tp), C.byref(sz)))
         u8 = torch.uint8
+        dev = ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch")
         self.tier_bufs = {f: torch.empty(max(int(getattr(sz, f)), 256), dtype=u8, device=self.device)
-                          for f in ("cache", "map", "owner", "ref", "freq", "ein", "queue", "scratch")}
+                          for f in dev + ("slot_stat",)}
         self.host_store = torch.empty(int(sz.host), dtype=u8).pin_memory()
-        tb = L.TierBuffers(*[self.tier_bufs[f].data_ptr() for f in ("cache", "map", "owner", "ref", "freq", "ein",
-                                                                      "queue", "scratch")],
-                           self.host_store.data_ptr())
+        tb = L.TierBuffers(*[self.tier_bufs[f].data_ptr() for f in dev], self.host_store.data_ptr(),
+                           self.tier_bufs["slot_stat"].data_ptr())
         L.check(lib.svf_tier_enable(self._h, C.byref(tp), C.byref(tb), _stream()))
         torch.cuda.synchronize(self.device)
 
     def reset_tier(self, M: int, qcap: int = 16384, promote_batch: int = 2048, sweep: int = 4, alpha: float = 0.6,
-                   beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp") -> None:
+                   beta: float = 0.4, theta0: float = 2.0, decay_every: int = 1 << 16, policy: str = "wavp",
+                   lrfu_lambda: float = 0.5) -> None:
         """Re-initialise the tiered store with new placement parameters (see
-        svf_tier_reset); M must stay the same."""
-        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every, L.TIER_POLICIES[policy], 0)
+        svf_tier_reset); M may shrink to any size up to the enabled one."""
+        tp = L.TierParams(M, qcap, promote_batch, sweep, alpha, beta, theta0, decay_every, L.TIER_POLICIES[policy],
+                          lrfu_lambda)
         L.check(L.load().svf_tier_reset(self._h, C.byref(tp), _stream()))
         torch.cuda.synchronize(self.device)
 
@@ -326,7 +331,7 @@ class Server:
         import math
         z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
         sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
-                            cfg.hash_log2, None, cfg.seed, None, None, None, cfg.t_every, cfg.W)
+                            cfg.hash_log2, None, cfg.seed, None, None, None, cfg.t_every, cfg.W, cfg.wpq, 0)
         r = L.Request(L.OP_SEARCH, Q.shape[0], Q.data_ptr(), sp, out_ids.data_ptr(), out_dist.data_ptr(), None, 0, 0,
                       tag, t_arrival)
         self._submit(r, (Q, out_ids, out_dist, cfg))

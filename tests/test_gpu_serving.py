@@ -436,3 +436,93 @@ def test_policy_admission_on_misses(svf, policy, queued):
     assert torch.equal(ia, ib) and torch.equal(da, db)
     assert ix.stats()["cache_misses"] > 0
     assert (int(ix.status.view(torch.int64)[11]) > 0) == queued
+
+
+@pytest.mark.parametrize("policy", ["lru", "lrfu"])
+def test_recency_policy_round(svf, policy):
+    """LRU / LRFU (the paper's Sec. 6.3 baselines): every queued miss is a
+    candidate, in miss order; the victims are the window's slots with the
+    oldest last hit (LRU) or the lowest C after folding the round's hits,
+    C <- C / 2 + hits with lambda = 1 (LRFU); an empty slot first, ties by
+    slot.  Checked against a plain host reference of the round."""
+    n, M, B = 4000, 256, 64
+    X, ix = built(svf, "u8", n, n, R=32)
+    ix.enable_tier(M=M, promote_batch=B, sweep=4, qcap=1024)
+    ix.reset_tier(M=M, promote_batch=B, sweep=4, qcap=1024, policy=policy, lrfu_lambda=1.0)
+    rng = np.random.default_rng(733)
+    owner = np.full(M, -1, np.int32)
+    cached = rng.choice(n, 230, replace=False)
+    slots = rng.choice(M, 230, replace=False)
+    owner[slots] = cached
+    map_ = np.full(n, -1, np.int32)
+    map_[cached] = slots
+    stat = np.zeros((M, 2), np.uint32)
+    if policy == "lru":
+        stat[:, 0] = rng.permutation(M).astype(np.uint32) + 1       # distinct last-hit stamps
+        stat[slots[:20], 0] = 7                                      # a tie, decided by slot
+    else:
+        stat[:, 0] = rng.integers(0, 4, M).astype(np.uint32)        # hits of the round
+        stat[:, 1] = (rng.integers(0, 16, M) * 0.25).astype(np.float32).view(np.uint32)  # C, exact halves
+    queue = rng.choice(np.setdiff1d(np.arange(n), cached), 150, replace=False).astype(np.uint32)
+    tb = ix.tier_bufs
+    tb["owner"][:M * 4].view(torch.int32).copy_(torch.from_numpy(owner))
+    tb["map"][:n * 4].view(torch.int32).copy_(torch.from_numpy(map_))
+    tb["slot_stat"][:M * 8].view(torch.int32).copy_(torch.from_numpy(stat.view(np.int32).reshape(-1)))
+    fq = np.zeros(n, np.uint32)
+    fq[queue] = np.uint32(1 << 31) | np.uint32(1)
+    tb["freq"][:n * 4].view(torch.int32).copy_(torch.from_numpy(fq.view(np.int32)))
+    tb["queue"][:150 * 4].view(torch.int32).copy_(torch.from_numpy(queue.view(np.int32)))
+    ix.status.view(torch.int64)[11] = 150
+    torch.cuda.synchronize()
+    got = ix.maintain()
+    # host reference of the round (window = 4 * B slots from hand 0)
+    if policy == "lrfu":
+        c = stat[:, 1].view(np.float32) * np.float32(0.5) + stat[:, 0].astype(np.float32)
+        stat[:, 1] = c.astype(np.float32).view(np.uint32)
+        stat[:, 0] = 0
+    keys = []
+    for s in range(4 * B):
+        if owner[s] < 0:
+            k = -1.0
+        else:
+            k = float(stat[s, 0]) if policy == "lru" else float(stat[s, 1:2].view(np.float32)[0])
+        keys.append((k, s))
+    victims = [s for _, s in sorted(keys)][:B]
+    for x, s in zip(queue[:B], victims):
+        if owner[s] >= 0:
+            map_[owner[s]] = -1
+        owner[s], map_[x] = x, s
+        if policy == "lru":
+            stat[s, 0] = 0  # this round's tick: no call has read the tier since the reset
+        else:
+            stat[s] = (0, np.float32(1.0).view(np.uint32))
+    assert got == B
+    np.testing.assert_array_equal(tb["owner"][:M * 4].view(torch.int32).cpu().numpy(), owner)
+    np.testing.assert_array_equal(tb["map"][:n * 4].view(torch.int32).cpu().numpy(), map_)
+    np.testing.assert_array_equal(tb["slot_stat"][:M * 8].view(torch.int32).cpu().numpy().view(np.uint32).reshape(M, 2),
+                                  stat)
+    cache = tb["cache"][:M * 128].view(M, 128).cpu().numpy()
+    for s in victims:
+        np.testing.assert_array_equal(cache[s], X[owner[s]])
+
+
+@pytest.mark.parametrize("policy", ["lru", "lrfu"])
+def test_recency_policies_keep_results(svf, policy):
+    """Whatever the placement, results equal the device-resident search; hits
+    stamp (LRU) or count (LRFU) the slot state, and a smaller cache after a
+    reset still serves every row."""
+    X, ix = built(svf, "u8", 5000, 5000, R=32)
+    Q = torch.from_numpy(synth.sample("u8", 400, 734)).cuda()
+    cfg = svf.SearchConfig(k=10, L=64, T=32, seed=5)
+    want = ix.search(Q, cfg)
+    ix.enable_tier(M=1000, theta0=0.5, promote_batch=256, qcap=4096)
+    ix.release_device_store()
+    for M in (1000, 300):
+        ix.reset_tier(M=M, promote_batch=256, qcap=4096, policy=policy)
+        for _ in range(3):
+            got = ix.search(Q, cfg)
+            assert torch.equal(got[0], want[0]) and torch.equal(got[1], want[1])
+            assert ix.maintain() > 0
+        st = ix.tier_bufs["slot_stat"][:M * 8].view(torch.int32).view(M, 2).cpu().numpy()
+        assert (st[:, 0] != 0).any() or (st[:, 1] != 0).any()
+        assert int((ix.tier_map()[:5000] >= 0).sum().item()) == M
