@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-rates", default="25,50,100,200")
     ap.add_argument("--serve-form", default="fp32", choices=["fp32", "fp8"],
                     help="serving traversal: fp32 rows through the tier, or a resident fp8 copy + exact re-rank")
+    ap.add_argument("--graph", default="exact", choices=["exact", "bootstrap"],
+                    help="unit96-10M graph: exact 2R-NN + prune of every row, or 200K exact + inserts")
     ap.add_argument("--cache-ratios", default="0.1",
                     help="cache sizes (fractions of n) of the placement ablation on a moving hot set (empty: skip)")
     ap.add_argument("--cache-policies", default="wavp,lru,lrfu",
@@ -99,31 +101,58 @@ def parse():
 
 
 # ---------------------------------------------------------------- setup
-def build_index(svf, torch, X, log_t, streams=1):
+def build_index(svf, torch, X, log_t, streams=1, graph="exact"):
+    """The unit96 index: graph "exact" = every row's exact 2R nearest
+    neighbours by inner product pruned to R (svf_build; the tensor-core scan
+    of the rows against themselves); "bootstrap" = the exact build of the
+    first 200,000 rows, then the rest inserted in batches of up to 1M."""
     n = X.shape[0]
-    # headroom for the serving streams' inserts
-    ix = svf.Index(96, n + 300_000 * streams, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"),
-                   max_batch=MAX_BATCH)
+    cap = n + 300_000 * streams
+    if graph == "exact":
+        ix = svf.Index(96, cap, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"), max_batch=n)
+        Xd = torch.from_numpy(X).cuda()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.build(Xd)
+        e1.record()
+        e1.synchronize()
+        del Xd
+        ix.build_s = e0.elapsed_time(e1) / 1e3
+        ix.build_fallback = ix.stats()["build_fallback"]
+        log_t("exact build", n, f"{ix.build_s:.1f} s", "rows by the exact scan:", ix.build_fallback)
+        ix.graph_desc = "exact 2R-NN by inner product (tensor cores, certified) pruned to R = 32 by RNG"
+        return ix
+    ix = svf.Index(96, cap, dtype="f32", metric="ip", R=R, lowp=("bf16", "fp8"), max_batch=MAX_BATCH)
     n0 = min(N_BOOT, n)
     t = time.time()
     ix.build(torch.from_numpy(X[:n0]).cuda())
     torch.cuda.synchronize()
     log_t("bootstrap build", n0, time.time() - t)
-    # inserts: host->device copy of each batch outside the timed region
-    ins_s = 0.0
     while ix.n_used < n:
         b = min(ix.n_used, MAX_BATCH, n - ix.n_used)
-        xb = torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda()
+        ix.insert(torch.from_numpy(X[ix.n_used:ix.n_used + b]).cuda(), L_ins=64, T_ins=48)
+    torch.cuda.synchronize()
+    ix.build_s, ix.build_fallback = None, None
+    ix.graph_desc = f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins=64, T_ins=48)"
+    return ix
+
+
+def insert_rate(svf, torch, ix, X_new, batch=MAX_BATCH):
+    """Insert throughput (Sec. 5.1 path) of batches of `batch` new vectors,
+    CUDA events around each svf_insert (host->device copies outside)."""
+    secs, done = 0.0, 0
+    for i in range(0, X_new.shape[0], batch):
+        xb = torch.from_numpy(X_new[i:i + batch]).cuda()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         ix.insert(xb, L_ins=64, T_ins=48)
         e1.record()
         e1.synchronize()
-        ins_s += e0.elapsed_time(e1) / 1e3
-    log_t("inserts", n - n0, ins_s)
-    ix.insert_rate = (n - n0) / ins_s if ins_s > 0 else None
-    return ix
+        secs += e0.elapsed_time(e1) / 1e3
+        done += xb.shape[0]
+    return done / secs
 
 
 def time_search(torch, ix, Q, cfg, reps=3):
@@ -166,7 +195,7 @@ def sweep(torch, ix, Q, gt, forms, grid, target, learned):
     return pts, best
 
 
-STOP_POINTS = [(64, 96), (64, 128), (128, 64), (128, 72), (128, 80), (128, 96)]
+STOP_POINTS = [(64, 48), (64, 56), (64, 64), (64, 72), (128, 64)]
 STOP_EVERY = 4
 
 
@@ -728,15 +757,16 @@ def main():
     ratios = [float(x) for x in a.cache_ratios.split(",") if x]
     cpols = [p for p in a.cache_policies.split(",") if p]
     # insert headroom: 300K rows per serving stream, 100K per ablation stream
-    ix = build_index(svf, torch, X, log_t, streams=5 + len(policies) + (len(ratios) * len(cpols) + 2) // 3)
+    ix = build_index(svf, torch, X, log_t, streams=6 + len(policies) + (len(ratios) * len(cpols) + 2) // 3,
+                     graph=a.graph)
     Xd = ix.vectors()[:a.n]
     Qe = torch.from_numpy(Qe_np).cuda()
     gt = exact_knn(svf, Xd, Qe, K, "ip")
     torch.cuda.synchronize()
     log_t("ground truth")
 
-    grid = [(64, 32), (64, 64), (64, 72), (64, 80), (64, 96), (128, 48), (128, 56), (128, 64), (128, 72), (128, 80),
-            (128, 96), (256, 96), (256, 128)]
+    grid = [(32, 40), (32, 48), (64, 32), (64, 36), (64, 38), (64, 40), (64, 44), (64, 48), (64, 56), (64, 64),
+            (64, 72), (64, 96), (128, 32), (128, 40), (128, 48), (128, 64), (128, 96), (256, 96), (256, 128)]
     # held-out calibration queries (the first tenth of the training queries):
     # every operating point is chosen on them, never on the timed batch
     ncal = a.ntrain // 10
@@ -859,6 +889,10 @@ def main():
     # ---- latency-bound batches: several warps per query (not timed above)
     sb = small_batch(svf, torch, ix, Qe, gt, cfg, a.target, sizes=(1, 16, 256, 1024))
     log_t("small batches", {W: {k: v for k, v in r.items() if k != "cfg"} for W, r in sb.items()})
+    # insert throughput: 1M new vectors in one batch (the later legs run on
+    # the grown index)
+    ins_rate = insert_rate(svf, torch, ix, synth.sample_chunked("unit96", MAX_BATCH, 303))
+    log_t("inserts/s", ins_rate)
 
     # ---- roofline of the search kernel (the only launch of a step)
     nq = a.nq
@@ -881,7 +915,7 @@ def main():
         "config": {"workload": unit96_name(a.n), "n": a.n, "d": 96, "R": R, "nq": nq, "k": K, "form": form,
                    "L": cfg.L, "T": cfg.T, "tau": getattr(cfg, "tau", None) if cfg.mlp is not None else None,
                    "recall@10": win["recall"], "l2": f"inputs larger than L2 ({a.n * 96 * 4 / 1e9:.1f} GB store, {a.n * R * 4 / 1e9:.1f} GB graph)",
-                   "graph": f"exact 2R-NN+prune of {N_BOOT} then inserts (L_ins=64, T_ins=48)"},
+                   "graph": ix.graph_desc, "build_s": ix.build_s, "build_rows_by_exact_scan": ix.build_fallback},
         "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "recall@10_calibration": v["recall_cal"],
                       "L": v["L"], "T": v["T"], "iters": v["iters"]} for k, v in best.items()},
         "operating_point": "each form's cheapest swept (L, T) with recall@10 >= target on 20,000 held-out "
@@ -1010,7 +1044,7 @@ def main():
     ix.delete(dels)
     torch.cuda.synchronize()
     t_del = time.time() - t_del
-    out["updates"] = {"inserts_per_s": ix.insert_rate, "insert_batch": MAX_BATCH, "L_ins": 64, "T_ins": 48,
+    out["updates"] = {"inserts_per_s": ins_rate, "insert_batch": MAX_BATCH, "L_ins": 64, "T_ins": 48,
                       "deletes_per_s": dels.numel() / t_del, "delete_batch": dels.numel(),
                       "repaired_rows": ix.stats()["repaired_rows"]}
     if rank == 0:

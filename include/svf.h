@@ -128,10 +128,7 @@ typedef struct {
  *             iterations, so a query expands up to W*T parents.  W > 1 does
  *             not combine with mlp / trace_feat / trace_meta (SVF_EINVAL).
  *             Meant for small batches, where one warp per query leaves most
- *             of the GPU idle.
- *   wpq       warps per query when W = 2: 0 as above (a CTA of W warps), or
- *             1: one warp expands both parents of an iteration (same results;
- *             twice the rows in flight per warp, for full batches). */
+ *             of the GPU idle. */
 typedef struct {
     int32_t k;
     int32_t L;
@@ -149,8 +146,6 @@ typedef struct {
     uint64_t *pool_out;
     int32_t t_every;
     int32_t W;
-    int32_t wpq;
-    int32_t reserved0;
 } svf_search_params;
 
 /* Running counters (since svf_create or svf_stats_reset). */
@@ -167,6 +162,7 @@ typedef struct {
     uint64_t cache_misses;      /* tiered store: rows read from host memory */
     uint64_t promoted;          /* tiered store: rows promoted into the cache */
     uint64_t evicted;           /* tiered store: cached rows evicted */
+    uint64_t build_fallback;    /* last build: rows whose tensor-core neighbours were recomputed by the exact scan */
 } svf_counters;
 
 typedef struct svf_index svf_index;
@@ -189,7 +185,11 @@ int svf_attach(svf_index *h, int64_t n_used);
  * of d primary elements (n <= n_cap, n <= max_batch).  Copies X into the
  * store, computes the exact 2R nearest neighbours of every row (self
  * excluded) and prunes each list to R (Sec. 5.1 reordering).  Resets
- * deletions; n_used = n. */
+ * deletions; n_used = n.  For an fp32 inner-product store with d <= 128,
+ * 2R <= 64 and n >= 65,536 the neighbours come from the tensor cores (bf16 tcgen05 scan of
+ * the rows against themselves, exact fp32 re-scoring of a certified band of
+ * candidates, the exact scan for rows whose certificate fails); otherwise
+ * from the exact SIMT scan.  Both give the exact 2R-NN by fp32 (distance, id). */
 int svf_build(svf_index *h, const void *X, int64_t n, void *stream);
 
 /* Search (Alg. 1): Q is device, nq rows of d elements (uint8 for a U8
@@ -380,7 +380,8 @@ int svf_tier_reset(svf_index *h, const svf_tier_params *tp, void *stream);
  * reads the row as it was and still treats the vertex as live (vertices an
  * update inserts have ids the older search never names).  One shadow per row
  * is kept: update E+1 starts once every search of an epoch below E has
- * finished.  An update that rewrites more than shadow_rows existing rows
+ * finished.  Searches of the versioned modes run without the stop network
+ * or traces (SVF_EINVAL).  An update that rewrites more than shadow_rows existing rows
  * (an insert of m vectors rewrites at most m*R; a delete's repair is counted
  * on the device) runs as a barrier instead.  `versions` is a device buffer of
  * svf_serve_version_bytes(h, shadow_rows) bytes, borrowed until stop.

@@ -52,14 +52,15 @@ class SearchParams(C.Structure):
                 ("rerank", C.c_int32), ("t_min", C.c_int32), ("mlp", C.c_void_p), ("z_tau", C.c_float),
                 ("hash_log2", C.c_int32), ("qkeys", C.c_void_p), ("seed", C.c_uint64), ("trace_feat", C.c_void_p),
                 ("trace_meta", C.c_void_p), ("pool_out", C.c_void_p), ("t_every", C.c_int32),
-                ("W", C.c_int32), ("wpq", C.c_int32), ("reserved0", C.c_int32)]
+                ("W", C.c_int32)]
 
 
 class Counters(C.Structure):
     _fields_ = [("n_used", C.c_int64), ("n_deleted", C.c_int64), ("search_queries", C.c_uint64),
                 ("search_iters", C.c_uint64), ("search_evals", C.c_uint64), ("hash_resets", C.c_uint64),
                 ("repaired_rows", C.c_uint64), ("reverse_targets", C.c_uint64), ("cache_hits", C.c_uint64),
-                ("cache_misses", C.c_uint64), ("promoted", C.c_uint64), ("evicted", C.c_uint64)]
+                ("cache_misses", C.c_uint64), ("promoted", C.c_uint64), ("evicted", C.c_uint64),
+                ("build_fallback", C.c_uint64)]
 
 
 class TierParams(C.Structure):

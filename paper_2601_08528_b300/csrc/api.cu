@@ -43,6 +43,11 @@ WsLayout svf::ws_layout(const svf_params &p, int64_t max_batch) {
     b += align256((size_t)max_batch * 2 * R * 8);
     w.knn_ids = b;
     b += align256((size_t)max_batch * 2 * R * 4);
+    w.tc = b;
+    w.tc_bytes = tc_build_applies(p.dtype, p.metric, p.d, max_batch, (int)(2 * R))
+                     ? tc_build_scratch_bytes(max_batch, p.d, (int)(2 * R))
+                     : 0;
+    b += align256(w.tc_bytes);
     // insert
     size_t in = 0;
     w.pool = in;
@@ -179,7 +184,16 @@ int svf_build(svf_index *h, const void *X, int64_t n, void *stream) {
     const int K = (int)(n - 1 < 2 * h->p.R ? n - 1 : 2 * h->p.R);
     if (K > 0) {
         uint64_t *keys = reinterpret_cast<uint64_t *>(h->wsp(h->ws.region + h->ws.knn_keys));
-        CUDA_TRY(launch_knn_self(P, n, 0, n, K, keys, st));
+        if (K == 2 * h->p.R && h->ws.tc_bytes && tc_build_applies(P.dtype, P.metric, P.d, n, K)) {
+            int64_t fb = 0;
+            rc = tc_build_knn(P, n, K, reinterpret_cast<uint8_t *>(h->wsp(h->ws.region + h->ws.tc)), h->ws.tc_bytes,
+                              keys, &fb, st);
+            if (rc) return rc;
+            h->build_fallback = fb;
+        } else {
+            CUDA_TRY(launch_knn_self(P, n, 0, n, K, keys, st));
+            h->build_fallback = 0;
+        }
         PruneArgs a{};
         a.X = P;
         a.cand = keys;
@@ -231,15 +245,10 @@ static int search_impl(svf_index *h, const void *Q, int64_t nq, const svf_search
     a.k = sp->k;
     a.T = sp->T;
     a.W = sp->W > 1 ? sp->W : 1;
-    a.wp = 1;
-    if (a.W == 2 && sp->wpq == 1) {  // one warp, two parents per iteration
-        a.W = 1;
-        a.wp = 2;
-    }
-    // up to W*R new ids per iteration (W parents); with W > 1 warps the
-    // default table holds about four iterations' ids, so resets stay as rare
-    // as with one parent per iteration
-    a.hash_bits = hash_bits_for(sp->L, a.W * a.wp * h->p.R, sp->hash_log2, a.W > 1 ? 4 : 1);
+    // up to W*R new ids per iteration (W parents); with W > 1 the default
+    // table holds about four iterations' ids, so resets stay as rare as with
+    // one parent per iteration
+    a.hash_bits = hash_bits_for(sp->L, a.W * h->p.R, sp->hash_log2, a.W > 1 ? 4 : 1);
     a.rerank = sp->rerank;
     a.out_dtype = h->p.dtype;
     a.out_ids = out_ids;
@@ -277,7 +286,6 @@ static int check_search(svf_index *h, const svf_search_params *sp, RowDesc *trav
         return fail(SVF_EINVAL, "W must be 0, 1, 2, 4 or 8");
     if (sp->W > 1 && (sp->mlp || sp->trace_feat || sp->trace_meta))
         return fail(SVF_EINVAL, "the stop network and traces run with one warp per query (W <= 1)");
-    if (sp->wpq != 0 && !(sp->wpq == 1 && sp->W == 2)) return fail(SVF_EINVAL, "wpq = 1 needs W = 2");
     *trav_out = trav;
     return SVF_OK;
 }
@@ -304,6 +312,8 @@ int svf::search_at(svf_index *h, const void *Q, int64_t nq, const svf_search_par
     if (!Q || !out_ids || !out_dist) return fail(SVF_EINVAL, "null Q / outputs");
     RowDesc trav{};
     if (int rc = check_search(h, sp, &trav)) return rc;
+    if (ver.row_ver && (sp->mlp || sp->trace_feat || sp->trace_meta))
+        return fail(SVF_EINVAL, "the stop network and traces are not available to searches that overlap updates");
     return search_impl(h, Q, nq, sp, out_ids, out_dist, st, n_used, trav, &ver);
 }
 
@@ -465,6 +475,7 @@ int svf_stats(svf_index *h, svf_counters *out) {
     out->cache_misses = s[kStMisses];
     out->promoted = s[kStPromoted];
     out->evicted = s[kStEvicted];
+    out->build_fallback = (uint64_t)h->build_fallback;
     return SVF_OK;
 }
 

@@ -36,9 +36,18 @@ inline void set_team(RowDesc &r) {
     r.cpl = (r.nchunk + ts - 1) / ts;
 }
 
+// Exact 2R-NN of the build on the tensor cores (tc_knn.cu): used for fp32
+// inner-product stores with d <= 128 and at least 2^16 rows; scratch inside
+// the workspace.
+bool tc_build_applies(int dtype, int metric, int d, int64_t n, int K);
+size_t tc_build_scratch_bytes(int64_t n, int d, int K);
+int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t bytes, uint64_t *keys,
+                 int64_t *out_fallback, cudaStream_t st);
+
 struct WsLayout {
     size_t head, vl, newrows, region, total;
     size_t knn_keys, knn_ids;        // build
+    size_t tc, tc_bytes;             // build on the tensor cores
     size_t pool, rows, dkeys, next;  // insert
     size_t cand;                     // delete
     int64_t max_batch;
@@ -105,6 +114,7 @@ struct svf_index {
     svf::WsLayout ws;
     int64_t n_used = 0;
     uint64_t repaired = 0;
+    int64_t build_fallback = 0;  // rows of the last build whose tensor-core certificate failed
     cudaStream_t last = nullptr;
     svf::Tier tier;
     svf::Consol cons;

@@ -16,18 +16,17 @@ cudaError_t launch_multi_fp8(const SearchArgs &a, int R, int W, int LW, size_t s
 
 constexpr size_t kSmemLimit = 232448;  // dynamic shared memory of one CTA (227 KB)
 
-// The staging buffer holds one iteration's worth of candidates (wp graph
-// rows); the final re-rank reuses it in chunks of whole primary rows (at
-// least 4).
+// The staging buffer holds one graph row's worth of candidates; the final
+// re-rank reuses it in chunks of whole primary rows (at least 4).
 size_t search_stage_bytes(const SearchArgs &a, int R) {
-    size_t cap = (size_t)R * (a.wp > 1 ? a.wp : 1) * a.trav.copy_bytes;
+    size_t cap = (size_t)R * a.trav.copy_bytes;
     if (a.rerank && cap < (size_t)4 * a.prim.copy_bytes) cap = (size_t)4 * a.prim.copy_bytes;
     return cap;
 }
 
 size_t search_warp_smem(int d, int L, int R, int hash_bits, size_t stage_bytes) {
     size_t q = ((size_t)d * 4 + 15) / 16 * 16;
-    size_t list = (size_t)(L > 2 * R ? L : 2 * R);  // >= the ids of two rows
+    size_t list = (size_t)(L > 2 * R ? L : 2 * R);
     return q + ((size_t)4 << hash_bits) + list * 4 + list * 8 + stage_bytes + 16;
 }
 

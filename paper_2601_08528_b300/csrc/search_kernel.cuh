@@ -151,16 +151,13 @@ __device__ __forceinline__ bool finish_pool(const SearchArgs &a, uint64_t (&pool
 
 // NCH > 0: the traversal rows are NCH 16-byte chunks (the launcher checks
 // the store against it); 0: any layout, read from a.trav at run time.
-// WP: parents expanded per iteration by the warp (the W nearest unexpanded
-// entries, Sec. 4.4's intra-query parallelism with W = WP; WP = 1 is Alg. 1):
-// their rows are filtered through the one visited table, staged and scored
-// together, and merged into the pool at once.
-template <int DT, int R, int LW, bool LEARN, int NCH, int WP>
+// VER: graph rows and deletions as of the search's epoch (a.ver), for
+// searches that overlap updates in the serving loop; the plain kernel reads
+// the current index.
+template <int DT, int R, int LW, bool LEARN, int NCH, bool VER>
 __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_kernel(const SearchArgs a) {
-    static_assert(WP == 1 || !LEARN, "the learned stop expands one parent per iteration");
     constexpr int L = 32 * LW;
-    constexpr int S = R / 32;  // graph ids per lane and row
-    constexpr int G = WP * S;  // graph ids per lane and iteration
+    constexpr int S = R / 32;  // graph ids per lane
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + wib;
@@ -208,7 +205,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         const int j = j0 + lane;
         // multiply-shift range reduction of the upper 32 random bits
         const uint32_t id = __umulhi((uint32_t)(splitmix64(base ^ (uint64_t)j) >> 32), (uint32_t)a.n_used);
-        bool ok = j < ndraw && !(a.ver.row_ver ? deleted_at(a.ver, a.del, id) : is_deleted(a.del, id));
+        bool ok = j < ndraw && !(VER ? deleted_at(a.ver, a.del, id) : is_deleted(a.del, id));
         uint32_t m = __match_any_sync(kFull, ok ? id : kEmpty);
         bool first = ok && ((m & lt_mask) == 0);
         bool acc = first && !ht_contains(ht, a.hash_bits, id);
@@ -251,7 +248,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
     }
 
     int iters = 0, evals = np, resets = 0, ran = 0;
-    const int reset_at = (1 << (a.hash_bits - 1)) - WP * R;
+    const int reset_at = (1 << (a.hash_bits - 1)) - R;
     for (int t = 0; t < a.T; t++) {
         if (hcount > reset_at) {
             ht_reset<LW>(ht, a.hash_bits, pool, lane);
@@ -260,61 +257,43 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
             for (int s = 0; s < LW; s++) hcount += __popc(__ballot_sync(kFull, !key_is_pad(pool[s])));
             resets++;
         }
-        // GetNearest: the first WP unexpanded entries in (distance, id) order
-        // (fewer when fewer remain); (ps, pl) is the first one's slot
-        int ps = -1, pl = 0, npar = 0;
-        uint32_t pid[WP];
-#pragma unroll
-        for (int w = 0; w < WP; w++) pid[w] = 0;
+        // GetNearest: the first unexpanded entry in (distance, id) order
+        int ps = -1, pl = 0;
 #pragma unroll
         for (int s = 0; s < LW; s++) {
-            uint32_t b = __ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0);
-#pragma unroll
-            for (int w = 0; w < WP; w++) {
-                if (npar < WP && b) {  // warp-uniform
-                    const int l = __ffs(b) - 1;
-                    b &= b - 1;
-                    const uint64_t pk = shfl64(pool[s], l);
-                    if (lane == l) pool[s] |= kExpBit;
-                    if (npar == 0) {
-                        ps = s;
-                        pl = l;
-                    }
-#pragma unroll
-                    for (int j = 0; j < WP; j++)
-                        if (j == npar) pid[j] = key_id(pk);
-                    npar++;
-                }
+            const uint32_t b = __ballot_sync(kFull, ((uint32_t)pool[s] & kExpBit) == 0);
+            if (ps < 0 && b) {
+                ps = s;
+                pl = __ffs(b) - 1;
             }
         }
-        if (npar == 0) break;  // nothing left to expand: the pool stays unchanged
-        iters += npar;
+        if (ps < 0) break;  // nothing left to expand: the pool stays unchanged
+        uint32_t pid = 0;
+        uint64_t pkey = 0;
+#pragma unroll
+        for (int s = 0; s < LW; s++)
+            if (s == ps) {
+                pkey = shfl64(pool[s], pl);
+                if (lane == pl) pool[s] |= kExpBit;
+            }
+        pid = key_id(pkey);
+        iters++;
 
         // FetchNeighbors + filter.  Unvisited ids are staged at once; the
         // deletion bits are read while the rows are in flight and deleted
         // ids are dropped before the merge (putting a deleted id in the
-        // visited table changes nothing: it never enters the pool).  With
-        // WP parents, an id in two rows is visited once.
-        uint32_t nb[G];
+        // visited table changes nothing: it never enters the pool).
+        uint32_t nb[S];
+        if constexpr (VER) {
+            versioned_row<S>(a.ver, a.graph, pid, lane, nb);
+        } else {
+            const uint32_t *row = a.graph + (int64_t)pid * R;
 #pragma unroll
-        for (int w = 0; w < WP; w++) {
-            uint32_t r[S];
-            if (w >= npar) {
-#pragma unroll
-                for (int s = 0; s < S; s++) r[s] = kEmpty;
-            } else if (a.ver.row_ver) {
-                versioned_row<S>(a.ver, a.graph, pid[w], lane, r);
-            } else {
-                const uint32_t *row = a.graph + (int64_t)pid[w] * R;
-#pragma unroll
-                for (int s = 0; s < S; s++) r[s] = __ldg(row + s * 32 + lane);
-            }
-#pragma unroll
-            for (int s = 0; s < S; s++) nb[w * S + s] = r[s];
+            for (int s = 0; s < S; s++) nb[s] = __ldg(row + s * 32 + lane);
         }
         int nf = 0;
 #pragma unroll
-        for (int s = 0; s < G; s++) {
+        for (int s = 0; s < S; s++) {
             const uint32_t v = nb[s];
             const bool fresh = v != kEmpty && (int64_t)v < a.n_used && ht_insert(ht, a.hash_bits, v);
             const uint32_t b = __ballot_sync(kFull, fresh);
@@ -323,25 +302,25 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         }
         hcount += nf;
         __syncwarp();
-        uint32_t dword[G];  // deletion-bitset words, consumed after the rows arrive
+        uint32_t dword[S];  // deletion-bitset words, consumed after the rows arrive
 #pragma unroll
-        for (int s = 0; s < G; s++) {
+        for (int s = 0; s < S; s++) {
             const int e = s * 32 + lane;
-            dword[s] = e < nf ? (a.ver.row_ver ? __ldcg(a.del + (list[e] >> 5)) : __ldg(a.del + (list[e] >> 5))) : 0u;
+            dword[s] = e < nf ? (VER ? __ldcg(a.del + (list[e] >> 5)) : __ldg(a.del + (list[e] >> 5))) : 0u;
         }
         const uint32_t newflag = learn ? kNewBit : 0u;
         if (!staged_dist<DT, NCH>(stg, a.trav, list, nf, keys, newflag, lane, qf, qb, tier, &hits, &misses)) {
             if (lane == 0) set_error(a.status, SVF_ETIMEOUT, qi);
             return;
         }
-        bool dflag[G];
+        bool dflag[S];
         int ndel = 0;
 #pragma unroll
-        for (int s = 0; s < G; s++) {
+        for (int s = 0; s < S; s++) {
             const int e = s * 32 + lane;
             dflag[s] = e < nf && ((dword[s] >> (list[e] & 31)) & 1u);
             // a deletion after the search's epoch leaves the vertex live for it
-            if (dflag[s] && a.ver.row_ver) dflag[s] = ld_relaxed_u32(a.ver.del_ep + list[e]) <= a.ver.epoch;
+            if (VER && dflag[s]) dflag[s] = ld_relaxed_u32(a.ver.del_ep + list[e]) <= a.ver.epoch;
             ndel += __popc(__ballot_sync(kFull, dflag[s]));
         }
         evals += nf - ndel;
@@ -359,10 +338,10 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
 
         // only candidates below the pool's current L-th key can enter
         const uint64_t worst = cmpk(shfl64(pool[LW - 1], 31));
-        uint64_t cand[G];
+        uint64_t cand[S];
         int nin = 0;
 #pragma unroll
-        for (int s = 0; s < G; s++) {
+        for (int s = 0; s < S; s++) {
             const int e = s * 32 + lane;
             cand[s] = (e < nf && !dflag[s]) ? keys[e] : kPad;
             if (cmpk(cand[s]) >= worst) cand[s] = kPad;
@@ -372,7 +351,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         if (nin > 0 && nin <= kFastInsert) {
             // most iterations admit a few candidates: insert them one by one
 #pragma unroll
-            for (int s = 0; s < G; s++) {
+            for (int s = 0; s < S; s++) {
                 uint32_t m = __ballot_sync(kFull, !key_is_pad(cand[s]));
                 while (m) {
                     const int src = __ffs(m) - 1;
@@ -381,9 +360,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
                 }
             }
         } else if (nin > 0) {
-            warp_sort<G>(cand, lane);
-            if constexpr (G <= LW) {
-                warp_merge_into<LW, G>(pool, cand, lane);
+            warp_sort<S>(cand, lane);
+            if constexpr (S <= LW) {
+                warp_merge_into<LW, S>(pool, cand, lane);
             } else {
                 // the best L of pool and candidates only need the best L candidates
                 uint64_t head[LW];
@@ -507,8 +486,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
     }
 }
 
-// Launch search_kernel<DT, R, LW, LEARN, NCH, WP> for a pool of 32 * LW.
-template <int DT, int R, bool LEARN, int NCH, int WP>
+// Launch search_kernel<DT, R, LW, LEARN, NCH, VER> for a pool of 32 * LW.
+template <int DT, int R, bool LEARN, int NCH, bool VER>
 cudaError_t launch_search_lw(const SearchArgs &a, int LW, size_t smem, cudaStream_t st) {
     const dim3 grid((unsigned)((a.nq + kSearchWarps - 1) / kSearchWarps)), block(kSearchWarps * 32);
     auto go = [&](auto kernel) {
@@ -518,10 +497,10 @@ cudaError_t launch_search_lw(const SearchArgs &a, int LW, size_t smem, cudaStrea
         return cudaGetLastError();
     };
     switch (LW) {
-    case 1: return go(search_kernel<DT, R, 1, LEARN, NCH, WP>);
-    case 2: return go(search_kernel<DT, R, 2, LEARN, NCH, WP>);
-    case 4: return go(search_kernel<DT, R, 4, LEARN, NCH, WP>);
-    case 8: return go(search_kernel<DT, R, 8, LEARN, NCH, WP>);
+    case 1: return go(search_kernel<DT, R, 1, LEARN, NCH, VER>);
+    case 2: return go(search_kernel<DT, R, 2, LEARN, NCH, VER>);
+    case 4: return go(search_kernel<DT, R, 4, LEARN, NCH, VER>);
+    case 8: return go(search_kernel<DT, R, 8, LEARN, NCH, VER>);
     }
     return cudaErrorInvalidValue;
 }
@@ -537,25 +516,27 @@ bool layout_is(const RowDesc &r) {
            r.cpl == (NCH + team_for(NCH, DT) - 1) / team_for(NCH, DT);
 }
 
-// Dispatch on R, learned features, parents per iteration and the row layout
+// Dispatch on R, learned features, versioned reads and the row layout
 // (specialised for the out-degree `RS` at d = 96 and d = 128; everything else
-// takes the generic kernel).  Two parents per iteration run without the
-// learned stop only.
+// takes the generic kernel).  Versioned reads run without the learned stop.
 template <int DT, int R, int NCH>
-cudaError_t launch_search_wp(const SearchArgs &a, int LW, bool learn, size_t smem, cudaStream_t st) {
-    if (learn) return launch_search_lw<DT, R, true, NCH, 1>(a, LW, smem, st);
-    return a.wp == 2 ? launch_search_lw<DT, R, false, NCH, 2>(a, LW, smem, st)
-                     : launch_search_lw<DT, R, false, NCH, 1>(a, LW, smem, st);
+cudaError_t launch_search_var(const SearchArgs &a, int LW, bool learn, size_t smem, cudaStream_t st) {
+    if (a.ver.row_ver) {
+        if (learn) return cudaErrorInvalidValue;
+        return launch_search_lw<DT, R, false, NCH, true>(a, LW, smem, st);
+    }
+    return learn ? launch_search_lw<DT, R, true, NCH, false>(a, LW, smem, st)
+                 : launch_search_lw<DT, R, false, NCH, false>(a, LW, smem, st);
 }
 template <int DT, int RS>
 cudaError_t launch_search_dtype(const SearchArgs &a, int R, int LW, bool learn, size_t smem, cudaStream_t st) {
     constexpr int N96 = nch_for_dim<DT>(96), N128 = nch_for_dim<DT>(128);
     if (R == RS) {
-        if (layout_is<DT, N96>(a.trav)) return launch_search_wp<DT, RS, N96>(a, LW, learn, smem, st);
-        if (layout_is<DT, N128>(a.trav)) return launch_search_wp<DT, RS, N128>(a, LW, learn, smem, st);
+        if (layout_is<DT, N96>(a.trav)) return launch_search_var<DT, RS, N96>(a, LW, learn, smem, st);
+        if (layout_is<DT, N128>(a.trav)) return launch_search_var<DT, RS, N128>(a, LW, learn, smem, st);
     }
-    if (R == 32) return launch_search_wp<DT, 32, 0>(a, LW, learn, smem, st);
-    if (R == 64) return launch_search_wp<DT, 64, 0>(a, LW, learn, smem, st);
+    if (R == 32) return launch_search_var<DT, 32, 0>(a, LW, learn, smem, st);
+    if (R == 64) return launch_search_var<DT, 64, 0>(a, LW, learn, smem, st);
     return cudaErrorInvalidValue;
 }
 

@@ -48,7 +48,7 @@ __device__ __forceinline__ void multi_gather(uint64_t (&pool)[LW], int n, int W,
     warp_sort<LW>(pool, lane);
 }
 
-template <int DT, int R, int LW, int NCH>
+template <int DT, int R, int LW, int NCH, bool VER>
 __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const SearchArgs a) {
     constexpr int L = 32 * LW;
     constexpr int S = R / 32;  // graph ids per lane
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
         for (int j0 = 0; j0 < ndraw && np < L && a.n_used > 0; j0 += 32) {
             const int j = j0 + lane;
             const uint32_t id = __umulhi((uint32_t)(splitmix64(base ^ (uint64_t)j) >> 32), (uint32_t)a.n_used);
-            bool ok = j < ndraw && !(a.ver.row_ver ? deleted_at(a.ver, a.del, id) : is_deleted(a.del, id));
+            bool ok = j < ndraw && !(VER ? deleted_at(a.ver, a.del, id) : is_deleted(a.del, id));
             uint32_t m = __match_any_sync(kFull, ok ? id : kEmpty);
             bool first = ok && ((m & lt_mask) == 0);
             bool acc = first && !ht_contains(ht, a.hash_bits, id);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
         //      append the keys that can enter the pool
         if (wid < npar) {
             uint32_t nb[S];
-            if (a.ver.row_ver) {
+            if constexpr (VER) {
                 versioned_row<S>(a.ver, a.graph, ctl->par[wid], lane, nb);
             } else {
                 const uint32_t *row = a.graph + (int64_t)ctl->par[wid] * R;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
 #pragma unroll
             for (int s = 0; s < S; s++) {
                 const int e = s * 32 + lane;
-                dword[s] = e < nf ? (a.ver.row_ver ? __ldcg(a.del + (list[e] >> 5)) : __ldg(a.del + (list[e] >> 5))) : 0u;
+                dword[s] = e < nf ? (VER ? __ldcg(a.del + (list[e] >> 5)) : __ldg(a.del + (list[e] >> 5))) : 0u;
             }
             if (!staged_dist<DT, NCH>(stg, a.trav, list, nf, keys, 0u, lane, qf, qb, tier, &hits, &misses)) {
                 if (lane == 0) {
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
                 const int e = s * 32 + lane;
                 bool live = e < nf && !((dword[s] >> (list[e] & 31)) & 1u);
                 // a deletion after the search's epoch leaves the vertex live for it
-                if (e < nf && !live && a.ver.row_ver) live = ld_relaxed_u32(a.ver.del_ep + list[e]) > a.ver.epoch;
+                if (VER && e < nf && !live) live = ld_relaxed_u32(a.ver.del_ep + list[e]) > a.ver.epoch;
                 nlive += __popc(__ballot_sync(kFull, live));
                 cand[s] = live ? keys[e] : kPad;
                 if (cmpk(cand[s]) >= worst) cand[s] = kPad;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kMultiMaxW * 32, 1) search_multi_kernel(const 
 }
 
 // Launch search_multi_kernel for W warps per query and a pool of 32 * LW.
-template <int DT, int R, int NCH>
+template <int DT, int R, int NCH, bool VER>
 cudaError_t launch_multi_lw(const SearchArgs &a, int W, int LW, size_t smem, cudaStream_t st) {
     const dim3 grid((unsigned)a.nq), block((unsigned)(32 * W));
     auto go = [&](auto kernel) {
@@ -298,24 +298,29 @@ cudaError_t launch_multi_lw(const SearchArgs &a, int W, int LW, size_t smem, cud
         return cudaGetLastError();
     };
     switch (LW) {
-    case 1: return go(search_multi_kernel<DT, R, 1, NCH>);
-    case 2: return go(search_multi_kernel<DT, R, 2, NCH>);
-    case 4: return go(search_multi_kernel<DT, R, 4, NCH>);
-    case 8: return go(search_multi_kernel<DT, R, 8, NCH>);
+    case 1: return go(search_multi_kernel<DT, R, 1, NCH, VER>);
+    case 2: return go(search_multi_kernel<DT, R, 2, NCH, VER>);
+    case 4: return go(search_multi_kernel<DT, R, 4, NCH, VER>);
+    case 8: return go(search_multi_kernel<DT, R, 8, NCH, VER>);
     }
     return cudaErrorInvalidValue;
 }
 
-// Dispatch on R and the row layout, as launch_search_dtype does.
+// Dispatch on R, versioned reads and the row layout, as launch_search_dtype does.
+template <int DT, int R, int NCH>
+cudaError_t launch_multi_var(const SearchArgs &a, int W, int LW, size_t smem, cudaStream_t st) {
+    return a.ver.row_ver ? launch_multi_lw<DT, R, NCH, true>(a, W, LW, smem, st)
+                         : launch_multi_lw<DT, R, NCH, false>(a, W, LW, smem, st);
+}
 template <int DT, int RS>
 cudaError_t launch_multi_dtype(const SearchArgs &a, int R, int W, int LW, size_t smem, cudaStream_t st) {
     constexpr int N96 = nch_for_dim<DT>(96), N128 = nch_for_dim<DT>(128);
     if (R == RS) {
-        if (layout_is<DT, N96>(a.trav)) return launch_multi_lw<DT, RS, N96>(a, W, LW, smem, st);
-        if (layout_is<DT, N128>(a.trav)) return launch_multi_lw<DT, RS, N128>(a, W, LW, smem, st);
+        if (layout_is<DT, N96>(a.trav)) return launch_multi_var<DT, RS, N96>(a, W, LW, smem, st);
+        if (layout_is<DT, N128>(a.trav)) return launch_multi_var<DT, RS, N128>(a, W, LW, smem, st);
     }
-    if (R == 32) return launch_multi_lw<DT, 32, 0>(a, W, LW, smem, st);
-    if (R == 64) return launch_multi_lw<DT, 64, 0>(a, W, LW, smem, st);
+    if (R == 32) return launch_multi_var<DT, 32, 0>(a, W, LW, smem, st);
+    if (R == 64) return launch_multi_var<DT, 64, 0>(a, W, LW, smem, st);
     return cudaErrorInvalidValue;
 }
 

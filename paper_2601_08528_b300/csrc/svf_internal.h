@@ -68,7 +68,6 @@ struct SearchArgs {
     uint32_t stage_bytes;
     size_t warp_smem;
     int W;            // warps (parents per iteration) per query; 1: one warp per query
-    int wp;           // with W = 1: parents per iteration of the one warp (1 or 2)
     VerCtx ver;       // versioned reads (searches overlapping updates), or ver.row_ver == null
 };
 

@@ -58,6 +58,14 @@ constexpr int SMEM_LIMIT = 232448;              // opt-in shared memory per bloc
 __host__ __device__ constexpr int smem_fixed(int kp) { return 1024 + TM * kp * 2 + LIST_BYTES + BUF_BYTES + BAR_BYTES; }
 __host__ __device__ constexpr int stage_bytes(int kp) { return TN * kp * 2; }
 static_assert(smem_fixed(KP) + 2 * stage_bytes(KP) <= SMEM_LIMIT, "two stages at the largest width");
+// Error bound of a bf16 product sum: each operand is rounded to bf16
+// (relative error <= 2^-9), so each product is off by at most
+// (2^-8 + 2^-18) |q_i x_i|, and the fp32 accumulation of d <= 128 products
+// adds at most d 2^-24 of the running sum: |error| <= c ||q|| ||x|| with c
+// about 0.0039 for inner products; 0.0085 leaves a margin of two (and the
+// squared-L2 form, -2 q.x, doubles it).
+constexpr float kBf16ErrC = 0.0085f;
+constexpr int64_t kTcBuildMinRows = 1 << 16;  // smaller builds take the SIMT scan
 constexpr int kSeedStride = 64;            // seed pass reads one tile in 64
 constexpr int kSeedRank = 8;               // seed = 8th best of the sample (~512th of all rows)
 constexpr int64_t kSeedMinRows = 1 << 17;  // smaller sets skip the seed pass
@@ -491,7 +499,7 @@ __global__ void rescore_kernel(const float *X, const float *Q, int d, int metric
     if (lane == 0) {
         // certificate: a row outside every slice's candidates has approx
         // distance >= bound, exact >= bound - eps
-        const float c = 0.0085f * (metric == SVF_L2 ? 2.f : 1.f);
+        const float c = kBf16ErrC * (metric == SVF_L2 ? 2.f : 1.f);
         const float eps = c * sqrtf(qn) * sqrtf(__uint_as_float(*maxnorm2));
         const float dk = k <= nreal ? fkey_inv((uint32_t)(out_keys[q * k + k - 1] >> 32)) : INFINITY;
         // L2 distances above carry no ||q||^2: add it to the approximate bound
@@ -513,6 +521,114 @@ __global__ void scatter_keys_kernel(const uint64_t *keys, const int32_t *idx, in
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m * k) return;
     out[(int64_t)idx[i / k] * k + i % k] = keys[i];
+}
+
+// Exact K nearest neighbours from the candidate lists when K is large (the
+// build's 2R): warp per query.  The candidates (lists x KC <= 32 NPL, the
+// query's own row excluded for a self join) are sorted by their approximate
+// distance a(x); only the band a(x) <= a_K + 2 eps is re-scored exactly, a_K
+// being the K-th smallest approximate distance: each of the K candidates
+// with a(x) <= a_K has exact distance <= a_K + eps, so the K-th exact
+// distance D_K <= a_K + eps, and a candidate outside the band has exact
+// distance > a_K + eps >= D_K.  The list certificate is the one of
+// rescore_kernel (rows outside every list have approximate distance >= the
+// smallest list bound); a query that fails it, or has fewer than K
+// candidates, is flagged for the exact SIMT scan.
+template <int NPL>
+__global__ void band_rescore_kernel(const float *X, int d, int metric, const unsigned int *maxnorm2, int lists,
+                                    const float *cand_d, const uint32_t *cand_i, int64_t q0, int64_t nq, int K,
+                                    float eps_c, uint64_t *out_keys, int32_t *flagged, unsigned long long *nflag) {
+    extern __shared__ float4 bq[];  // per warp: the query row (d <= 128 floats)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (q >= nq) return;
+    const int nc = lists * KC;
+    const uint32_t self = (uint32_t)(q0 + q);
+    const float *qr = X + (q0 + q) * d;
+    float4 *qs = bq + wib * (KP / 4);
+    for (int c = lane; c < d / 4; c += 32) qs[c] = reinterpret_cast<const float4 *>(qr)[c];
+    __syncwarp();
+    float qn = 0.f;
+    for (int c = lane; c < d; c += 32) qn = fmaf(qr[c], qr[c], qn);
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) qn += __shfl_xor_sync(kFull, qn, m);
+    float bound = INFINITY;
+    for (int s = lane; s < lists; s += 32) bound = fminf(bound, cand_d[(q * lists + s) * KC + KC - 1]);
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) bound = fminf(bound, __shfl_xor_sync(kFull, bound, m));
+    uint64_t ak[NPL];
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        const int e = s * 32 + lane;
+        const uint32_t id = e < nc ? cand_i[q * nc + e] : kEmpty;
+        ak[s] = (id == kEmpty || id == self) ? kPad : make_key(fkey(cand_d[q * nc + e]), id);
+    }
+    warp_sort<NPL>(ak, lane);
+    const float c = eps_c * (metric == SVF_L2 ? 2.f : 1.f);
+    const float eps = c * sqrtf(qn) * sqrtf(__uint_as_float(*maxnorm2));
+    uint64_t akK = kPad;
+#pragma unroll
+    for (int s = 0; s < NPL; s++)
+        if (s == ((K - 1) >> 5)) akK = shfl64(ak[s], (K - 1) & 31);
+    bool fail = key_is_pad(akK);
+    int nb = 0;
+    if (!fail) {
+        const float cut = fkey_inv((uint32_t)(akK >> 32)) + 2.f * eps;
+        // the band is a prefix of the sorted candidates
+#pragma unroll
+        for (int s = 0; s < NPL; s++)
+            nb += __popc(__ballot_sync(kFull, !key_is_pad(ak[s]) && fkey_inv((uint32_t)(ak[s] >> 32)) <= cut));
+#pragma unroll
+        for (int s = 0; s < NPL; s++) {
+            const int e = s * 32 + lane;
+            uint64_t kx = kPad;
+            if (e < nb) {
+                // the row in 16-byte loads, summed in element order
+                const uint32_t id = key_id(ak[s]);
+                const float4 *xr = reinterpret_cast<const float4 *>(X + (int64_t)id * d);
+                float acc = 0.f;
+#pragma unroll 8
+                for (int c4 = 0; c4 < d / 4; c4++) {
+                    const float4 x = __ldg(xr + c4), qv = qs[c4];
+                    if (metric == SVF_IP) {
+                        acc = fmaf(qv.x, x.x, acc);
+                        acc = fmaf(qv.y, x.y, acc);
+                        acc = fmaf(qv.z, x.z, acc);
+                        acc = fmaf(qv.w, x.w, acc);
+                    } else {
+                        acc = fmaf(qv.x - x.x, qv.x - x.x, acc);
+                        acc = fmaf(qv.y - x.y, qv.y - x.y, acc);
+                        acc = fmaf(qv.z - x.z, qv.z - x.z, acc);
+                        acc = fmaf(qv.w - x.w, qv.w - x.w, acc);
+                    }
+                }
+                kx = make_key(fkey(metric == SVF_IP ? -acc : acc), id);
+            }
+            ak[s] = kx;
+        }
+        warp_sort<NPL>(ak, lane);
+        uint64_t dK = kPad;
+#pragma unroll
+        for (int s = 0; s < NPL; s++)
+            if (s == ((K - 1) >> 5)) dK = shfl64(ak[s], (K - 1) & 31);
+        const float DK = fkey_inv((uint32_t)(dK >> 32));
+        const float b = metric == SVF_L2 ? bound + qn : bound;
+        fail = key_is_pad(dK) || (!(b - eps > DK) && isfinite(bound));
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        const int e = s * 32 + lane;
+        if (e < K) out_keys[q * K + e] = fail ? kPad : ak[s];
+    }
+    if (fail && lane == 0) {
+        const unsigned long long p = atomicAdd(nflag, 1ull);
+        flagged[p] = (int32_t)q;
+    }
+}
+
+__global__ void self_ids_kernel(const int32_t *idx, int64_t m, int64_t q0, int64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = q0 + idx[i];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -561,6 +677,64 @@ int split_count(int64_t n, int64_t nq) {
     return (int)best;
 }
 
+// The approximate pass over bf16 rows xb [n][kp] for bf16 queries qb [nq][kp]:
+// a seed pass over every kSeedStride-th tile for large n, then the full pass
+// into cand_d / cand_i [nq][2 * splits][KC].  splits: at least min_splits,
+// else split_count's choice, at most 64.
+struct TcPass {
+    const __nv_bfloat16 *xb, *qb;
+    int64_t n, nq;
+    int kp, metric;
+    const float *norms;
+    float *cd, *seed;
+    uint32_t *ci;
+    unsigned long long *status;
+    int splits;  // out
+};
+
+int tc_pass(TcPass &p, int min_splits, int max_splits, cudaStream_t st) {
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, const_cast<__nv_bfloat16 *>(p.qb), p.nq, p.kp, TM) ||
+        !make_map(&tb, const_cast<__nv_bfloat16 *>(p.xb), p.n, p.kp, TN))
+        return fail(SVF_ECUDA, "cuTensorMapEncodeTiled is unavailable or rejected the layout");
+    TcArgs a{};
+    a.n = p.n;
+    a.nq = p.nq;
+    a.metric = p.metric;
+    a.atoms = p.kp / KA;
+    a.norms = p.norms;
+    a.cand_d = p.cd;
+    a.cand_i = p.ci;
+    a.status = p.status;
+    a.ns = std::min(NS_MAX, (SMEM_LIMIT - smem_fixed(p.kp)) / stage_bytes(p.kp));
+    const int smem = smem_fixed(p.kp) + a.ns * stage_bytes(p.kp);
+    CUDA_TRY(cudaFuncSetAttribute(tc_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const unsigned qtiles = (unsigned)((p.nq + TM - 1) / TM);
+    a.splits = std::min(max_splits, std::max(min_splits, split_count(p.n, p.nq)));
+    a.rows_per_split = ((p.n + a.splits - 1) / a.splits + TN - 1) / TN * TN;
+    a.tile_stride = 1;
+    if (p.n >= kSeedMinRows) {
+        // Seed pass: every kSeedStride-th tile, one slice (few, long lists:
+        // an unseeded list pays for its first insertions).  The r-th best of
+        // that sample sits near rank r * kSeedStride of the whole set, a
+        // threshold most rows of the full pass then fail at once.
+        TcArgs s1 = a;
+        s1.splits = 1;
+        s1.rows_per_split = (p.n + TN - 1) / TN * TN;
+        s1.tile_stride = kSeedStride;
+        s1.seed = nullptr;
+        tc_knn_kernel<<<dim3(qtiles, 1), THREADS, smem, st>>>(ta, tb, s1);
+        CUDA_TRY(cudaGetLastError());
+        seed_kernel<<<(unsigned)((p.nq + 127) / 128), 128, 0, st>>>(p.cd, p.nq, HALVES, kSeedRank, p.seed);
+        CUDA_TRY(cudaGetLastError());
+        a.seed = p.seed;
+    }
+    tc_knn_kernel<<<dim3(qtiles, (unsigned)a.splits), THREADS, smem, st>>>(ta, tb, a);
+    CUDA_TRY(cudaGetLastError());
+    p.splits = a.splits;
+    return SVF_OK;
+}
+
 struct TcLayout {
     size_t xb, qb, norms, maxn, cd, ci, keys, flagged, nflag, gq, gk, seed, total;
 };
@@ -591,7 +765,132 @@ TcLayout tc_layout(int64_t n, int64_t nq, int k, int d) {
     return L;
 }
 
+// ---------------------------------------------------------------- build
+// Slices of the build's scan: 2 * splits lists of KC candidates hold four
+// times the K neighbours wanted, so each list's bound lies far beyond them.
+constexpr int kBuildNPL = 8;                    // candidates per lane in band_rescore_kernel (<= 256)
+int build_splits(int K) { return std::max(1, (4 * K + 2 * KC - 1) / (2 * KC)); }
+
+struct TcBuildLayout {
+    size_t xb, norms, maxn, cd, ci, seed, flagged, nflag, gq, gk, gself, total;
+    int64_t chunk;
+};
+
+TcBuildLayout tc_build_layout(int64_t n, int d, int K) {
+    TcBuildLayout L{};
+    const int kp = (d + KA - 1) / KA * KA;
+    L.chunk = std::min<int64_t>(std::max<int64_t>(n, 1), 131072);
+    const int lists = 2 * build_splits(K);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    L.xb = take((size_t)n * kp * 2);
+    L.norms = take((size_t)n * 4);
+    L.maxn = take(256);
+    L.cd = take((size_t)L.chunk * lists * KC * 4);
+    L.ci = take((size_t)L.chunk * lists * KC * 4);
+    L.seed = take((size_t)L.chunk * 4);
+    L.flagged = take((size_t)L.chunk * 4);
+    L.nflag = take(256);
+    L.gq = take((size_t)L.chunk * d * 4);
+    L.gk = take((size_t)L.chunk * K * 8);
+    L.gself = take((size_t)L.chunk * 8);
+    L.total = o;
+    return L;
+}
+
 }  // namespace
+
+// Inner product only: for squared L2 the bound eps grows with ||q|| ||x||,
+// which for data far from the origin exceeds the gaps between neighbour
+// distances, so the certificate would fail for most rows.
+bool tc_build_applies(int dtype, int metric, int d, int64_t n, int K) {
+    return dtype == SVF_F32 && metric == SVF_IP && d % 16 == 0 && d <= KP && n >= kTcBuildMinRows && K >= 1 &&
+           2 * build_splits(K) * KC <= 32 * kBuildNPL && n < (1ll << 31);
+}
+
+size_t tc_build_scratch_bytes(int64_t n, int d, int K) { return tc_build_layout(n, d, K).total; }
+
+// Exact K nearest neighbours (self excluded) of every row of an fp32 store,
+// sorted by (distance, id): the tensor-core scan of the rows against
+// themselves in chunks of queries, band re-scoring with its certificate,
+// and the exact SIMT scan for the queries that fail it.
+int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t bytes, uint64_t *keys,
+                 int64_t *out_fallback, cudaStream_t st) {
+    const int d = X.d, kp = (d + KA - 1) / KA * KA;
+    const TcBuildLayout L = tc_build_layout(n, d, K);
+    if (bytes < L.total) return fail(SVF_EINVAL, "build scratch of %zu bytes, need %zu", bytes, L.total);
+    const float *Xf = reinterpret_cast<const float *>(X.base);
+    auto *xb = reinterpret_cast<__nv_bfloat16 *>(scratch + L.xb);
+    float *norms = reinterpret_cast<float *>(scratch + L.norms);
+    unsigned int *maxn = reinterpret_cast<unsigned int *>(scratch + L.maxn);
+    float *cd = reinterpret_cast<float *>(scratch + L.cd);
+    uint32_t *ci = reinterpret_cast<uint32_t *>(scratch + L.ci);
+    int32_t *flagged = reinterpret_cast<int32_t *>(scratch + L.flagged);
+    unsigned long long *nflag = reinterpret_cast<unsigned long long *>(scratch + L.nflag);
+    unsigned long long *status = nflag + 8;
+    to_bf16_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(Xf, n, d, kp, xb, norms);
+    CUDA_TRY(cudaMemsetAsync(maxn, 0, 4, st));
+    CUDA_TRY(cudaMemsetAsync(status, 0, 8, st));
+    max_kernel<<<296, 256, 0, st>>>(norms, n, maxn);
+    const int splits = build_splits(K);
+    const int wpb = 4;
+    const size_t bsm = (size_t)wpb * KP * 4;
+    int64_t fallback = 0;
+    for (int64_t q0 = 0; q0 < n; q0 += L.chunk) {
+        const int64_t nq = std::min(L.chunk, n - q0);
+        TcPass pass{};
+        pass.xb = xb;
+        pass.qb = xb + q0 * kp;  // the queries are rows of the store (16-byte aligned: kp is a multiple of 32)
+        pass.n = n;
+        pass.nq = nq;
+        pass.kp = kp;
+        pass.metric = X.metric;
+        pass.norms = norms;
+        pass.cd = cd;
+        pass.ci = ci;
+        pass.seed = reinterpret_cast<float *>(scratch + L.seed);
+        pass.status = status;
+        if (int rc = tc_pass(pass, splits, splits, st)) return rc;
+        CUDA_TRY(cudaMemsetAsync(nflag, 0, 8, st));
+        band_rescore_kernel<kBuildNPL><<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, bsm, st>>>(
+            Xf, d, X.metric, maxn, 2 * splits, cd, ci, q0, nq, K, kBf16ErrC, keys + q0 * K, flagged, nflag);
+        CUDA_TRY(cudaGetLastError());
+        unsigned long long hf[2] = {0, 0};
+        CUDA_TRY(cudaMemcpyAsync(&hf[0], nflag, 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&hf[1], status, 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (hf[1]) return fail(SVF_ETIMEOUT, "build: a tensor-core pipeline wait gave up");
+        const int64_t m = (int64_t)hf[0];
+        if (m > 0) {
+            float *gq = reinterpret_cast<float *>(scratch + L.gq);
+            uint64_t *gk = reinterpret_cast<uint64_t *>(scratch + L.gk);
+            int64_t *gself = reinterpret_cast<int64_t *>(scratch + L.gself);
+            gather_rows_kernel<<<(unsigned)((m * d + 255) / 256), 256, 0, st>>>(Xf + q0 * d, d, flagged, m, gq);
+            self_ids_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(flagged, m, q0, gself);
+            KnnArgs ka{};
+            ka.X = X;
+            ka.n = n;
+            ka.Q = gq;
+            ka.q_row_bytes = d * 4;
+            ka.nq = m;
+            ka.self = gself;
+            ka.self_base = -1;
+            ka.k = K;
+            ka.out_keys = gk;
+            CUDA_TRY(launch_knn(ka, st));
+            scatter_keys_kernel<<<(unsigned)((m * K + 255) / 256), 256, 0, st>>>(gk, flagged, m, K, keys + q0 * K);
+            CUDA_TRY(cudaGetLastError());
+            fallback += m;
+        }
+    }
+    if (out_fallback) *out_fallback = fallback;
+    return SVF_OK;
+}
+
 }  // namespace svf
 
 using namespace svf;
@@ -630,47 +929,24 @@ int svf_knn_tc(const float *X, int64_t n, int32_t d, int32_t metric, const float
     CUDA_TRY(cudaMemsetAsync(maxn, 0, 4, st));
     CUDA_TRY(cudaMemsetAsync(nflag, 0, 8, st));
     max_kernel<<<296, 256, 0, st>>>(norms, n, maxn);
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, qb, nq, kp, TM) || !make_map(&tb, xb, n, kp, TN))
-        return fail(SVF_ECUDA, "cuTensorMapEncodeTiled is unavailable or rejected the layout");
-    TcArgs a{};
-    a.n = n;
-    a.nq = nq;
-    a.metric = metric;
-    a.atoms = kp / KA;
-    a.norms = norms;
-    a.cand_d = cd;
-    a.cand_i = ci;
     // the status word of a stand-alone call lives in the flag counter's slot
     unsigned long long *status = nflag + 8;
     CUDA_TRY(cudaMemsetAsync(status, 0, 8, st));
-    a.status = status;
-    a.ns = std::min(NS_MAX, (SMEM_LIMIT - smem_fixed(kp)) / stage_bytes(kp));
-    const int smem = smem_fixed(kp) + a.ns * stage_bytes(kp);
-    CUDA_TRY(cudaFuncSetAttribute(tc_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const unsigned qtiles = (unsigned)((nq + TM - 1) / TM);
-    a.splits = split_count(n, nq);
-    a.rows_per_split = ((n + a.splits - 1) / a.splits + TN - 1) / TN * TN;
-    a.tile_stride = 1;
-    if (n >= kSeedMinRows) {
-        // Seed pass: every kSeedStride-th tile, one slice (few, long lists:
-        // an unseeded list pays for its first insertions).  The r-th best of
-        // that sample sits near rank r * kSeedStride of the whole set, a
-        // threshold most rows of the full pass then fail at once.
-        float *seed = reinterpret_cast<float *>(S + L.seed);
-        TcArgs s1 = a;
-        s1.splits = 1;
-        s1.rows_per_split = (n + TN - 1) / TN * TN;
-        s1.tile_stride = kSeedStride;
-        s1.seed = nullptr;
-        tc_knn_kernel<<<dim3(qtiles, 1), THREADS, smem, st>>>(ta, tb, s1);
-        CUDA_TRY(cudaGetLastError());
-        seed_kernel<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(cd, nq, HALVES, kSeedRank, seed);
-        CUDA_TRY(cudaGetLastError());
-        a.seed = seed;
-    }
-    tc_knn_kernel<<<dim3(qtiles, (unsigned)a.splits), THREADS, smem, st>>>(ta, tb, a);
-    CUDA_TRY(cudaGetLastError());
+    TcPass pass{};
+    pass.xb = xb;
+    pass.qb = qb;
+    pass.n = n;
+    pass.nq = nq;
+    pass.kp = kp;
+    pass.metric = metric;
+    pass.norms = norms;
+    pass.cd = cd;
+    pass.ci = ci;
+    pass.seed = reinterpret_cast<float *>(S + L.seed);
+    pass.status = status;
+    if (int rc = tc_pass(pass, 1, 64, st)) return rc;
+    TcArgs a{};
+    a.splits = pass.splits;
     const int wpb = 4;
     const size_t rsm = (size_t)wpb * a.splits * HALVES * KC * 8;
     CUDA_TRY(cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));

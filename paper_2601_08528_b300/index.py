@@ -38,7 +38,6 @@ class SearchConfig:
     t_min: int = 4
     t_every: int = 1
     W: int = 1     # parents per iteration = warps per query (1, 2, 4, 8)
-    wpq: int = 0   # 1: with W = 2, one warp expands both parents (full batches)
 
 
 class Index:
@@ -144,7 +143,7 @@ class Index:
         z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
         sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
                             cfg.hash_log2, _ptr(qkeys), cfg.seed, _ptr(trace_feat), _ptr(trace_meta), _ptr(pool_out),
-                            cfg.t_every, cfg.W, cfg.wpq, 0)
+                            cfg.t_every, cfg.W)
         L.check(L.load().svf_search(self._h, _ptr(Q), nq, C.byref(sp), _ptr(out_ids), _ptr(out_dist),
                                     _stream(stream)))
         return out_ids, out_dist
@@ -331,7 +330,7 @@ class Server:
         import math
         z_tau = math.log(cfg.tau / (1.0 - cfg.tau)) if cfg.mlp is not None else 0.0
         sp = L.SearchParams(cfg.k, cfg.L, cfg.T, prec, int(cfg.rerank), cfg.t_min, _ptr(cfg.mlp), z_tau,
-                            cfg.hash_log2, None, cfg.seed, None, None, None, cfg.t_every, cfg.W, cfg.wpq, 0)
+                            cfg.hash_log2, None, cfg.seed, None, None, None, cfg.t_every, cfg.W)
         r = L.Request(L.OP_SEARCH, Q.shape[0], Q.data_ptr(), sp, out_ids.data_ptr(), out_dist.data_ptr(), None, 0, 0,
                       tag, t_arrival)
         self._submit(r, (Q, out_ids, out_dist, cfg))

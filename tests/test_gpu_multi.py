@@ -148,40 +148,3 @@ def test_multi_rejects_bad_arguments(svf, orc):
     with pytest.raises(svf.SvfError):
         ix.search(Q, svf.SearchConfig(k=10, L=64, W=2, mlp=net))
 
-
-@pytest.mark.parametrize("mix,metric,R,L,T,prec", [("u8", "l2", 64, 64, 16, None), ("u8", "l2", 32, 128, 40, None),
-                                                   ("u8", "l2", 32, 32, 12, None), ("tiny", "l2", 32, 64, 20, None),
-                                                   ("unit96", "ip", 32, 64, 20, "fp8"),
-                                                   ("unit96", "ip", 32, 128, 30, "bf16")])
-def test_one_warp_two_parents(svf, orc, mix, metric, R, L, T, prec):
-    """W = 2 expanded by one warp per query (wpq = 1): the same W-parent
-    search as the oracle's (uint8 bit-exact, fp32 rule otherwise) and as the
-    two-warp CTA, with deletions and visited-table resets in the mix."""
-    X, st, g = setup(orc, mix, 3000, R, metric, 721)
-    n = len(X)
-    dele = synth.pick_live_ids(n, None, 150, 722)
-    bits = orc.bitset(n, dele)
-    Q = synth.sample(mix, 300, 723)
-    lowp = (prec,) if prec else ()
-    ix = make_index(svf, X, g, metric, R, lowp=lowp, deleted=dele)
-    low = prec is not None
-    base = dict(k=10, L=L, T=T, seed=9, W=2, precision=prec, rerank=low)
-    one = ix.search(torch.from_numpy(Q).cuda(), svf.SearchConfig(**base, wpq=1))
-    ix.stats_reset()
-    small = ix.search(torch.from_numpy(Q).cuda(), svf.SearchConfig(**base, wpq=1, hash_log2=8))
-    s = ix.stats()
-    two = ix.search(torch.from_numpy(Q).cuda(), svf.SearchConfig(**base))
-    assert torch.equal(one[0], two[0]) and torch.equal(one[1], two[1])
-    assert torch.equal(one[0], small[0]) and torch.equal(one[1], small[1])
-    assert s["hash_resets"] > 0
-    if low:
-        o = orc.search(orc.Store.from_vectors(X, metric, dtype=prec), n, g, bits, Q, 10, L, T, 9, want_pool=True, W=2)
-        ref = P.rerank_ref(orc, st, Q, o, 10)
-    else:
-        ref = o = orc.search(st, n, g, bits, Q, 10, L, T, 9, W=2)
-    if mix == "u8":
-        P.check_exact(one[0].cpu().numpy(), one[1].cpu().numpy(), ref)
-    else:
-        P.check_fp32(one[0].cpu().numpy(), one[1].cpu().numpy(), ref, X, Q, metric)
-    assert s["search_iters"] == o["iters"].sum()
-    assert not np.isin(P.as_u32(one[0].cpu().numpy()), dele).any()

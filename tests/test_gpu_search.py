@@ -185,3 +185,34 @@ def test_codecs_bit_exact(svf, orc):
     got = f8.cpu().numpy()
     want = orc.fp8_encode_rows(X)
     np.testing.assert_array_equal(got[:, :100], want[:, :100])
+
+
+@pytest.mark.parametrize("mix,metric", [("unit96", "ip"), ("tiny", "l2")])
+def test_build_on_tensor_cores_rows_sampled(svf, orc, mix, metric):
+    """At n >= 65,536 fp32 inner-product rows the build's exact 2R-NN come
+    from the tensor cores (certified bf16 scan + exact fp32 band re-scoring,
+    SIMT scan for the rows that fail the certificate); squared L2 keeps the
+    SIMT scan.  Sampled rows equal the oracle's exact 64-NN + RNG prune,
+    except where the oracle met a near tie."""
+    n, R = 70_000, 32
+    X = synth.sample(mix, n, 281)
+    ix = svf.Index(X.shape[1], n, dtype="f32", metric=metric, R=R, max_batch=n)
+    ix.build(torch.from_numpy(X).cuda())
+    g = P.as_u32(ix.graph[:n].cpu().numpy())
+    s = ix.stats()
+    assert s["build_fallback"] < (n // 10 if metric == "ip" else 1)
+    vs = np.sort(np.random.default_rng(282).choice(n, 400, replace=False))
+    st = orc.Store.from_vectors(X, metric)
+    ids, d, kgap = orc.knn(st, X[vs], 2 * R, self_ids=vs.astype(np.int64))
+    differ = 0
+    for i, v in enumerate(vs):
+        row, pgap = orc.prune(st, ids[i], d[i], R)
+        if not np.array_equal(g[v], row):
+            differ += 1
+            assert min(kgap[i], pgap) <= P.TOL, f"row {v} differs without a near tie"
+    assert differ <= len(vs) // 20
+    # no self loops or repeats, every row full
+    assert not (g == np.arange(n)[:, None]).any()
+    srt = np.sort(g, 1)
+    assert not ((srt[:, 1:] == srt[:, :-1]) & (srt[:, 1:] != 0xFFFFFFFF)).any()
+    assert (g != 0xFFFFFFFF).all()
