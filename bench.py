@@ -67,6 +67,9 @@ def parse():
                     help="serving traversal: fp32 rows through the tier, or a resident fp8 copy + exact re-rank")
     ap.add_argument("--graph", default="exact", choices=["exact", "bootstrap"],
                     help="unit96-10M graph: exact 2R-NN + prune of every row, or 200K exact + inserts")
+    ap.add_argument("--u8", type=int, default=1, help="also measure the 1M x 128 uint8 configuration (0: skip)")
+    ap.add_argument("--fixed-point", default="",
+                    help="form,L,T: time that form at that point only, without the stop networks (profiling)")
     ap.add_argument("--cache-ratios", default="0.1",
                     help="cache sizes (fractions of n) of the placement ablation on a moving hot set (empty: skip)")
     ap.add_argument("--cache-policies", default="wavp,lru,lrfu",
@@ -195,7 +198,7 @@ def sweep(torch, ix, Q, gt, forms, grid, target, learned):
     return pts, best
 
 
-STOP_POINTS = [(64, 48), (64, 56), (64, 64), (64, 72), (128, 64)]
+STOP_POINTS = [(64, 40), (64, 44), (64, 48), (64, 56), (64, 64)]
 STOP_EVERY = 4
 
 
@@ -350,6 +353,60 @@ def job_rate(units_per_rank, world, seconds):
     """Whole-job throughput: the units all ranks processed over the max-over-
     ranks time (weak scaling: every rank has its own batch)."""
     return world * units_per_rank / seconds
+
+
+def u8_leg(svf, torch, log_t, n=1_000_000, nq=10_000, R8=64, batches=10, batch=10_000):
+    """The integer-exact configuration: n uint8 vectors, d = 128, squared L2
+    exact in int32, out-degree 64 (exact 128-NN + RNG prune), 10,000 queries
+    at L = 64 and 128 (T = L / 2), then a 10 % insert stream in batches of
+    10,000 (L_ins = 128, T_ins = 64).  Search QPS with the HBM roofline of
+    its launch, inserts/s, and the oracle timed on the same queries."""
+    X = synth.sample_chunked("u8", n + batches * batch, 201)
+    Q_np = synth.sample_chunked("u8", nq, 202)
+    ix = svf.Index(128, n + batches * batch, dtype="u8", metric="l2", R=R8, max_batch=n)
+    torch.cuda.synchronize()
+    t = time.time()
+    ix.build(torch.from_numpy(X[:n]).cuda())
+    torch.cuda.synchronize()
+    out = {"workload": f"u8-1M: {n} x 128 uint8 (1,024-centre mixture), squared L2 exact in int32, R = {R8}",
+           "build_s": time.time() - t}
+    Q = torch.from_numpy(Q_np).cuda()
+    gt = svf.knn(ix.vectors()[:n], Q, K, "l2")[0]
+    from paper_2601_08528_b300.learned import recall_at_k
+    peaks, _ = measured_peaks()
+    for L in (64, 128):
+        cfg = svf.SearchConfig(k=K, L=L, T=L // 2)
+        ix.stats_reset()
+        ids, _ = ix.search(Q, cfg)
+        s = ix.stats()
+        sec = time_search(torch, ix, Q, cfg, reps=5)
+        alg = s["search_iters"] * R8 * 4 + s["search_evals"] * 128 + nq * (128 + K * 8)
+        out[f"L{L}"] = {"T": L // 2, "recall@10": recall_at_k(ids, gt), "qps": nq / sec, "ms": 1e3 * sec,
+                        "iters_per_query": s["search_iters"] / nq, "evals_per_query": s["search_evals"] / nq,
+                        "roofline": {"achieved_gbs": alg / sec / 1e9, "frac": alg / sec / 1e9 / peaks["hbm_gbs"]}}
+        log_t("u8", L, json.dumps(out[f"L{L}"]))
+    secs = 0.0
+    for b in range(batches):
+        xb = torch.from_numpy(X[n + b * batch:n + (b + 1) * batch]).cuda()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.insert(xb, L_ins=128, T_ins=64)
+        e1.record()
+        e1.synchronize()
+        secs += e0.elapsed_time(e1) / 1e3
+    out["inserts_per_s"] = batches * batch / secs
+    out["insert_stream"] = f"{batches} batches of {batch}, L_ins = 128, T_ins = 64"
+    # the oracle on the host cores, the same queries at L = 64 on the built graph
+    import oracle as orc
+    g_np = ix.graph[:n].cpu().numpy().view(np.uint32)
+    st = orc.Store.from_vectors(X[:n], "l2")
+    t = time.time()
+    orc.search(st, n, g_np, None, Q_np, K, 64, 32, 0x5F0C)
+    out["cpu_baseline"] = {"value": nq / (time.time() - t), "unit": "queries/s", "cores": orc.threads(),
+                           "kind": "oracle", "sample": f"all {nq} queries at L = 64, T = 32"}
+    ix.close()
+    return out
 
 
 def unit96_name(n):
@@ -801,23 +858,41 @@ def main():
         print(json.dumps(out), flush=True)
         return 0
 
-    # learned stop: traces of the plain search of training queries
-    Qtr = torch.from_numpy(Qtr_np).cuda()
-    nets = train_stops(torch, svf, ix, Qtr, gt_cal, ncal, ["bf16", "fp8"])
-    del Qtr, Qtr_np
-    log_t("stop networks")
     forms = [("fp32", svf.SearchConfig(k=K)),
              ("bf16+rerank", svf.SearchConfig(k=K, precision="bf16", rerank=True)),
              ("fp8+rerank", svf.SearchConfig(k=K, precision="fp8", rerank=True)),
              ("bf16+rerank+stop", svf.SearchConfig(k=K, precision="bf16", rerank=True)),
              ("fp8+rerank+stop", svf.SearchConfig(k=K, precision="fp8", rerank=True))]
+    if a.fixed_point:
+        # one form at a given (L, T), no stop networks (profiling runs)
+        fname, fl, ft = a.fixed_point.split(",")
+        forms, grid, nets = [f for f in forms if f[0] == fname], [(int(fl), int(ft))], {}
+    else:
+        # learned stop: traces of the plain search of training queries
+        Qtr = torch.from_numpy(Qtr_np).cuda()
+        nets = train_stops(torch, svf, ix, Qtr, gt_cal, ncal, ["bf16", "fp8"])
+        del Qtr
+        log_t("stop networks")
+    del Qtr_np
     pts, best = select_points(torch, ix, forms, grid, a.target, nets, Qcal, gt_cal, Qe, gt)
     log_t("sweep")
+    if not best and a.fixed_point:
+        best = {p["form"]: dict(p, recall_cal=p["recall"]) for p in pts}
     if not best:
         raise SystemExit("no form reached the recall target")
     lowp = {k: v for k, v in best.items() if k != "fp32"}
     win = max(lowp.values() if lowp else best.values(), key=lambda p: p["qps"])
     cfg = win["cfg"]
+    # what any stop rule could save at the headline point: a stop after the
+    # last iteration that changed each query's top 10 (traces of the timed
+    # queries) against the iterations the fixed-T search runs
+    _, meta = lrn.capture_traces(ix, Qe, dataclasses.replace(cfg, mlp=None))
+    ran, last = meta[:, 0].double(), meta[:, 1].double()
+    stop_bound = {"L": cfg.L, "T": cfg.T, "form": win["form"], "iters_fixed_T": ran.mean().item(),
+                  "iters_perfect_stop": (last + 1).clamp(min=1).mean().item(),
+                  "last_change_p50": last.median().item(), "last_change_p90": last.quantile(0.9).item()}
+    stop_bound["saving_bound"] = 1.0 - stop_bound["iters_perfect_stop"] / stop_bound["iters_fixed_T"]
+    log_t("stop bound", json.dumps(stop_bound))
 
     # ---- timed region: `steps` launches of the winning form
     st = torch.cuda.current_stream()
@@ -918,13 +993,14 @@ def main():
                    "graph": ix.graph_desc, "build_s": ix.build_s, "build_rows_by_exact_scan": ix.build_fallback},
         "forms": {k: {"qps": v["qps"], "recall@10": v["recall"], "recall@10_calibration": v["recall_cal"],
                       "L": v["L"], "T": v["T"], "iters": v["iters"]} for k, v in best.items()},
+        "stop_bound": stop_bound,
         "operating_point": "each form's cheapest swept (L, T) with recall@10 >= target on 20,000 held-out "
                            "calibration queries; recall and QPS measured on the 10,000 timed queries",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(form, cfg.L, cfg.T),
                      "peak_source": src,
                      "alg_bytes_per_launch": alg, "iters_per_launch": iters, "evals_per_launch": evals,
-                     "hash_resets": s["hash_resets"]},
+                     "hash_resets_per_launch": s["hash_resets"] / a.steps},
         "e2e": {"value": job_rate(nq * a.steps, world, e2e_t), "unit": "queries/s",
                 "h2d_bytes_per_step": Qh.numel() * 4, "d2h_bytes_per_step": ids_h.numel() * 4 + d_h.numel() * 4},
         "gpu_launches": a.steps,
@@ -1047,6 +1123,8 @@ def main():
     out["updates"] = {"inserts_per_s": ins_rate, "insert_batch": MAX_BATCH, "L_ins": 64, "T_ins": 48,
                       "deletes_per_s": dels.numel() / t_del, "delete_batch": dels.numel(),
                       "repaired_rows": ix.stats()["repaired_rows"]}
+    if a.u8 and rank == 0:
+        out["u8_1M"] = u8_leg(svf, torch, log_t)
     if rank == 0:
         # oracle timed on host cores: the headline form at the headline (L, T)
         # (a stop form is timed without its network, i.e. for the full T)
