@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--serve-small", type=int, default=1,
                     help="serve128-50M: latency-bound search batches run with several warps per query, W by "
                          "batch size from a measurement before tiering (0: one warp per query throughout)")
+    ap.add_argument("--serve-barrier", action="store_true",
+                    help="serve128-50M: also run each rate's stream in the barrier consistency mode")
     ap.add_argument("--serve-compare", action="store_true",
                     help="serve128-50M: also run each rate's stream with one warp per query throughout")
     ap.add_argument("--raw-rates", default="500,2000,5000,10000",
@@ -752,7 +754,7 @@ def serve_main(a, svf, torch, log_t):
     del X
     log_t("tiered", slots)
     X_ins = synth.sample_chunked("serve128", 1_500_000, 503)
-    res, res1 = [], []
+    res, res1, resb = [], [], []
     for i, rate in enumerate(float(x) for x in a.serve_rates.split(",")):
         r = serve_stream(svf, torch, ix, "serve128", X_ins[i * 300_000:(i + 1) * 300_000], rate, a.serve_seconds,
                          2.0, 510 + i, cfg, small=small)
@@ -764,6 +766,12 @@ def serve_main(a, svf, torch, log_t):
                              a.serve_seconds, 2.0, 510 + i, cfg)
             res1.append(r)
             log_t("rate one warp", rate, json.dumps(r))
+        if a.serve_barrier:
+            # the same stream with every update a barrier
+            r = serve_stream(svf, torch, ix, "serve128", X_ins[i * 300_000:(i + 1) * 300_000], rate,
+                             a.serve_seconds, 2.0, 510 + i, cfg, small=small, consistency="barrier")
+            resb.append(r)
+            log_t("rate barrier", rate, json.dumps(r))
     p99 = [x["latency_ms"]["search"]["p99"] for x in res if x["latency_ms"]["search"]["p99"] is not None]
     out = {"metric": "serving p99 search latency (ms) at offered load", "value": min(p99) if p99 else None,
            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
@@ -778,6 +786,8 @@ def serve_main(a, svf, torch, log_t):
            "rates": res}
     if res1:
         out["rates_one_warp"] = res1
+    if resb:
+        out["rates_barrier"] = resb
     print(json.dumps(out), flush=True)
     return 0
 
