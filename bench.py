@@ -630,13 +630,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def csrc_hash():
+def csrc_hash(root=None):
+    """Hash of the library's code: every source under csrc/ with comments and
+    blank lines removed, so that a comment edit does not mark a profile of
+    unchanged kernels as stale."""
     import glob
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2601_08528_b300", "csrc", "*"))):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(glob.glob(os.path.join(root or ROOT, "paper_2601_08528_b300", "csrc", "*"))):
+        with open(f, encoding="utf-8") as fh:
+            txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in txt.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -22,8 +22,8 @@
 //    distances and the best k by (distance, id) are kept.  A certificate
 //    checks the result: every row left out of a list has an approximate
 //    distance at least that list's 16th, and the bf16 error of a distance is
-//    at most c ||q|| ||x|| (two roundings of 2^-9 each per product, plus the
-//    fp32 sums; c = 0.0085 covers d <= 128 with margin, doubled for L2), so
+//    at most c ||q|| ||x|| (two roundings of 2^-8 each per product, plus the
+//    fp32 sums; c = 0.0085 covers d <= 128, doubled for L2), so
 //    if min_list(16th) - eps exceeds the k-th exact distance no row can be
 //    missing.  Queries that fail it are recomputed by the SIMT kernel
 //    (knn.cu).
@@ -58,11 +58,11 @@ constexpr int SMEM_LIMIT = 232448;              // opt-in shared memory per bloc
 __host__ __device__ constexpr int smem_fixed(int kp) { return 1024 + TM * kp * 2 + LIST_BYTES + BUF_BYTES + BAR_BYTES; }
 __host__ __device__ constexpr int stage_bytes(int kp) { return TN * kp * 2; }
 static_assert(smem_fixed(KP) + 2 * stage_bytes(KP) <= SMEM_LIMIT, "two stages at the largest width");
-// Error bound of a bf16 product sum: each operand is rounded to bf16
-// (relative error <= 2^-9), so each product is off by at most
-// (2^-8 + 2^-18) |q_i x_i|, and the fp32 accumulation of d <= 128 products
-// adds at most d 2^-24 of the running sum: |error| <= c ||q|| ||x|| with c
-// about 0.0039 for inner products; 0.0085 leaves a margin of two (and the
+// Error bound of a bf16 product sum: each operand is rounded to bf16 (8-bit
+// significand, relative error <= 2^-8), so each product is off by at most
+// (2^-7 + 2^-16) |q_i x_i|, and the fp32 accumulation of d <= 128 products
+// adds at most about d 2^-23 of their magnitude: |error| <= c ||q|| ||x||
+// with c = 0.0079 for inner products; 0.0085 keeps a margin above that (the
 // squared-L2 form, -2 q.x, doubles it).
 constexpr float kBf16ErrC = 0.0085f;
 constexpr int64_t kTcBuildMinRows = 1 << 16;  // smaller builds take the SIMT scan

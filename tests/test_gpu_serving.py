@@ -526,3 +526,49 @@ def test_recency_policies_keep_results(svf, policy):
         st = ix.tier_bufs["slot_stat"][:M * 8].view(torch.int32).view(M, 2).cpu().numpy()
         assert (st[:, 0] != 0).any() or (st[:, 1] != 0).any()
         assert int((ix.tier_map()[:5000] >= 0).sum().item()) == M
+
+
+def test_server_updates_beyond_the_shadow_capacity(svf):
+    """An insert that would rewrite more rows than the version buffer holds
+    (here 100 vectors x R = 32 rows > 1,000 shadow rows) runs as a barrier;
+    the results still equal the same searches run alone at their epochs, and
+    the graph equals the one built alone."""
+    n0, ncap = 6000, 9000
+    X, ix = built(svf, "u8", n0, ncap, R=32, max_batch=6000)
+    _, ref_ix = built(svf, "u8", n0, ncap, R=32, max_batch=6000)
+    rng = np.random.default_rng(751)
+    reqs = _trace(rng, 90, n0, X, n0)
+    cfg = svf.SearchConfig(k=10, L=64, T=32)
+    comps, outs, upd, n_used = _serve_trace(svf, ix, X, n0, reqs, cfg, "snapshot", shadow_rows=1000)
+    by_epoch = _check_epochs(reqs, comps, "snapshot")
+    epoch = 0
+    for tag, (op, a, b) in enumerate(reqs + [("end", 0, 0)]):
+        if op == "search":
+            continue
+        for t in by_epoch.pop(epoch, []):
+            Q, oi, od = outs[t]
+            ri, rd = ref_ix.search(Q, cfg)
+            assert torch.equal(ri, oi) and torch.equal(rd, od), f"request {t} at epoch {epoch}"
+        if op == "end":
+            break
+        kind, v = upd[tag]
+        if kind == "insert":
+            ref_ix.insert(v, L_ins=64, T_ins=32)
+        else:
+            ref_ix.delete(v)
+        epoch += 1
+    torch.cuda.synchronize()
+    assert torch.equal(ix.graph[:n_used], ref_ix.graph[:n_used])
+
+
+def test_server_rejects_bad_consistency_setup(svf):
+    from paper_2601_08528_b300 import _lib as L
+    X, ix = built(svf, "u8", 2000, 2000, R=32)
+    with pytest.raises(KeyError):
+        svf.Server(ix, consistency="eventual")
+    import ctypes as C
+    h = C.c_void_p()
+    cfg = L.ServeCfg(4, 2, 64, 2, None, 0, 1000)  # snapshot mode without a version buffer
+    assert L.load().svf_serve_start(ix._h, C.byref(cfg), C.byref(h)) == L.SVF_EINVAL
+    cfg = L.ServeCfg(4, 2, 64, 7, None, 0, 0)
+    assert L.load().svf_serve_start(ix._h, C.byref(cfg), C.byref(h)) == L.SVF_EINVAL
