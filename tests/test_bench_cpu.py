@@ -39,3 +39,22 @@ def test_serving_picks_the_first_range_that_holds_the_batch():
     assert [bench.pick_cfg(pol, s, "w1") for s in (1, 16, 17, 256, 257, 1024, 1025, 2048)] == \
         ["w8", "w8", "w4", "w4", "w2", "w2", "w1", "w1"]
     assert bench.pick_cfg(None, 5, "w1") == "w1" and bench.pick_cfg([], 5, "w1") == "w1"
+
+
+def test_profiled_traffic_follows_the_kernel_code(tmp_path):
+    """The committed ncu summary's DRAM bytes are reported only for the
+    captured form and point and while the library's code (comments aside)
+    hashes to the captured value."""
+    import shutil
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "paper_2601_08528_b300", "csrc"), root / "paper_2601_08528_b300" / "csrc")
+    h0 = bench.csrc_hash(str(root))
+    assert h0 == bench.csrc_hash()
+    f = root / "paper_2601_08528_b300" / "csrc" / "svf_dev.cuh"
+    f.write_text(f.read_text() + "\n// a comment changes nothing\n/* nor does\n   this */\n")
+    assert bench.csrc_hash(str(root)) == h0
+    f.write_text(f.read_text() + "\nnamespace svf { constexpr int kProbe = 1; }\n")
+    assert bench.csrc_hash(str(root)) != h0
+    assert bench.profiled_traffic("fp8+rerank", 64, 40) is not None  # the committed capture
+    assert bench.profiled_traffic("fp8+rerank", 64, 72) is None      # another launch point
+    assert bench.profiled_traffic("bf16+rerank", 64, 40) is None     # another form
