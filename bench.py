@@ -996,6 +996,21 @@ def main():
     mean_launch = total / a.steps
     peaks, src = measured_peaks()
     achieved = alg / mean_launch / 1e9
+    # the random-row fetch ceiling: the kernel's own copy pattern over uniform
+    # random rows of the traversal store, nothing computed (svf_gather_probe)
+    tstore, tpitch, trow = ((ix.vecs_fp8, 128, 112) if form.startswith("fp8") else
+                            (ix.vecs_bf16, 192, 192) if form.startswith("bf16") else (ix.vecs, 384, 384))
+    fetched = iters + evals + (nq * cfg.L if cfg.rerank else 0)
+    by_w = {}
+    for wps in (16, 24, 32):
+        got, ms = svf.gather_probe(tstore, ix.n_used, tpitch, trow, int(evals), warps_per_sm=wps, seed=11 + wps)
+        by_w[wps] = got / (ms / 1e3)
+    best_w = max(by_w, key=by_w.get)
+    gather = {"rows_per_s": by_w[best_w], "row_bytes": trow, "warps_per_sm": best_w,
+              "rows_per_s_by_warps_per_sm": {str(w): v for w, v in by_w.items()},
+              "kernel_rows_per_s": fetched / mean_launch, "frac": fetched / mean_launch / by_w[best_w],
+              "note": "kernel rows = graph rows + traversal rows + re-rank rows per launch, each one random fetch"}
+    log_t("gather ceiling", gather)
     out = {
         "metric": METRIC,
         "value": job_rate(nq * a.steps, world, total),
@@ -1016,7 +1031,7 @@ def main():
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(form, cfg.L, cfg.T),
                      "peak_source": src,
                      "alg_bytes_per_launch": alg, "iters_per_launch": iters, "evals_per_launch": evals,
-                     "hash_resets_per_launch": s["hash_resets"] / a.steps},
+                     "hash_resets_per_launch": s["hash_resets"] / a.steps, "gather_ceiling": gather},
         "e2e": {"value": job_rate(nq * a.steps, world, e2e_t), "unit": "queries/s",
                 "h2d_bytes_per_step": Qh.numel() * 4, "d2h_bytes_per_step": ids_h.numel() * 4 + d_h.numel() * 4},
         "gpu_launches": a.steps,

@@ -510,6 +510,25 @@ int svf_mlp_forward(const float *params, const float *feat, int64_t n, float *z,
 uint32_t svf_wait_limit(void);
 int svf_selftest_wait_timeout(uint32_t polls, unsigned long long *status, double *out_seconds, void *stream);
 
+/* ---- random-row fetch ceiling (a measurement, no counterpart in the paper).
+ * The search fetches rows at ids it cannot predict (Alg. 1's neighbour
+ * expansion), so the rate at which the GPU serves independent random rows
+ * bounds it.  svf_gather_probe copies about `rows` rows of `row_bytes` bytes,
+ * at ids drawn uniformly from [0, n) of a device table whose rows are `pitch`
+ * bytes apart, into shared memory with the search kernel's own copy pattern:
+ * one 1-D bulk copy per lane, 32 rows per warp batch on one mbarrier, blocks
+ * of 4 warps, `warps_per_sm` warps per SM; nothing is computed on the rows.
+ * Outputs (host): *out_rows = rows actually copied (`rows` rounded up to whole
+ * batches of every warp), *out_ms = device time of the launch (CUDA events on
+ * `stream`).  table: device, 16-byte aligned, n * pitch bytes, read only;
+ * pitch and row_bytes multiples of 16 with 16 <= row_bytes <= min(pitch,
+ * 1024); 1 <= n < 2^31; rows >= 1; warps_per_sm a multiple of 4 in [4, 64];
+ * status: caller-owned device buffer of >= 2 uint64 (overwritten).
+ * Errors: SVF_EINVAL (arguments), SVF_ETIMEOUT (a bounded wait gave up;
+ * recorded in status), SVF_ECUDA. */
+int svf_gather_probe(const void *table, int64_t n, int32_t pitch, int32_t row_bytes, int64_t rows, int32_t warps_per_sm,
+                     uint64_t seed, unsigned long long *status, int64_t *out_rows, float *out_ms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

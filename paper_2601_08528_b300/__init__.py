@@ -5,4 +5,4 @@ The compute lives in ``libsvf.so`` (CUDA kernels behind the C ABI of
 buffers with torch and passes pointers.
 """
 from ._lib import EMPTY, SvfError, load  # noqa: F401
-from .index import Index, SearchConfig, Server, knn, knn_tc  # noqa: F401
+from .index import Index, SearchConfig, Server, gather_probe, knn, knn_tc  # noqa: F401

@@ -27,7 +27,7 @@ SYMBOLS = ["svf_last_error", "svf_buffer_sizes", "svf_create", "svf_destroy", "s
            "svf_mlp_forward", "svf_tier_buffer_sizes", "svf_tier_enable", "svf_tier_maintain", "svf_tier_theta", "svf_tier_reset",
            "svf_serve_now", "svf_serve_version_bytes", "svf_serve_start", "svf_serve_submit", "svf_serve_poll", "svf_serve_drain",
            "svf_serve_stop", "svf_knn_tc_scratch_bytes", "svf_knn_tc", "svf_wait_limit", "svf_selftest_wait_timeout",
-           "svf_knn_static", "svf_knn_static_capacity", "svf_knn_static_error"]
+           "svf_knn_static", "svf_knn_static_capacity", "svf_knn_static_error", "svf_gather_probe"]
 
 
 class Params(C.Structure):
@@ -165,6 +165,7 @@ def load() -> C.CDLL:
         "svf_knn_static": (I32, [P, I64, I32, I32, I32, P, I64, P, I32, P, P, P]),
         "svf_knn_static_capacity": (I64, []),
         "svf_knn_static_error": (C.c_char_p, []),
+        "svf_gather_probe": (I32, [P, I64, I32, I32, I64, I32, U64, P, C.POINTER(C.c_int64), C.POINTER(C.c_float), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

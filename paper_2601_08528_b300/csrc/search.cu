@@ -17,7 +17,8 @@ cudaError_t launch_multi_fp8(const SearchArgs &a, int R, int W, int LW, size_t s
 constexpr size_t kSmemLimit = 232448;  // dynamic shared memory of one CTA (227 KB)
 
 // The staging buffer holds one graph row's worth of candidates; the final
-// re-rank reuses it in chunks of whole primary rows (at least 4).
+// re-rank stages whole primary rows (at least 4 at a time) into it and the
+// visited table beside it.
 size_t search_stage_bytes(const SearchArgs &a, int R) {
     size_t cap = (size_t)R * a.trav.copy_bytes;
     if (a.rerank && cap < (size_t)4 * a.prim.copy_bytes) cap = (size_t)4 * a.prim.copy_bytes;

@@ -29,8 +29,9 @@ namespace svf {
 // Stop-network inference (16 -> 64 relu -> 1) reads the packed bf16 layout
 // of mlp.cu: W1 [64][16], b1 [64], w2 [64], b2.
 
-// Up to this many admitted candidates are inserted one at a time (rank by
-// ballot, shift by shuffle); more are sorted and merged.
+// Up to this many admitted candidates are placed into the pool directly
+// (ranks by ballots, scattered through shared memory); more are sorted and
+// merged.  The multi-warp kernel inserts up to this many one at a time.
 constexpr int kFastInsert = 8;
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t id, int bits) { return (id * 0x9E3779B1u) >> (32 - bits); }
@@ -163,14 +164,16 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
     const int64_t qi = (int64_t)blockIdx.x * kSearchWarps + wib;
     if (qi >= a.nq) return;
 
+    // per warp: query, ids, keys, then the visited table and the staging
+    // buffer side by side (the final re-rank stages rows into both)
     uint8_t *my = smem + (size_t)wib * a.warp_smem;
     float *qf = reinterpret_cast<float *>(my);
     uint8_t *qb = my;
-    uint32_t *ht = reinterpret_cast<uint32_t *>(my + a.q_bytes);
-    uint32_t *list = ht + (1 << a.hash_bits);
+    uint32_t *list = reinterpret_cast<uint32_t *>(my + a.q_bytes);
     uint64_t *keys = reinterpret_cast<uint64_t *>(list + a.list_len);
+    uint32_t *ht = reinterpret_cast<uint32_t *>(keys + a.list_len);
     Stage stg;
-    stg.buf = reinterpret_cast<uint8_t *>(keys + a.list_len);
+    stg.buf = reinterpret_cast<uint8_t *>(ht + (1 << a.hash_bits));
     stg.cap = a.stage_bytes;
     stg.mbar = reinterpret_cast<uint64_t *>(stg.buf + a.stage_bytes);
     stg.phase[0] = stg.phase[1] = 0;
@@ -349,16 +352,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         }
         nf -= ndel;
         if (nin > 0 && nin <= kFastInsert) {
-            // most iterations admit a few candidates: insert them one by one
-#pragma unroll
-            for (int s = 0; s < S; s++) {
-                uint32_t m = __ballot_sync(kFull, !key_is_pad(cand[s]));
-                while (m) {
-                    const int src = __ffs(m) - 1;
-                    m &= m - 1;
-                    warp_insert_one<LW>(pool, shfl64(cand[s], src), lane);
-                }
-            }
+            // most iterations admit a few candidates: place them directly
+            // (the keys buffer is free: the candidates are in registers)
+            warp_insert_few<LW, S>(pool, cand, keys, lane);
         } else if (nin > 0) {
             warp_sort<S>(cand, lane);
             if constexpr (S <= LW) {
@@ -469,6 +465,10 @@ __global__ void __launch_bounds__(kSearchWarps * 32, SVF_SEARCH_MINB) search_ker
         }
     }
 
+    // the visited table is no longer needed: the re-rank stages rows into it
+    // and the staging buffer after it, so fewer rounds of copies
+    stg.buf = reinterpret_cast<uint8_t *>(ht);
+    stg.cap = a.stage_bytes + (4u << a.hash_bits);
     if (!finish_pool<LW>(a, pool, list, keys, stg, qf, qb, lane, qi, hits, misses)) return;
     if (a.trace_meta && lane == 0) {
         a.trace_meta[qi * 2 + 0] = ran;

@@ -165,6 +165,64 @@ __device__ __forceinline__ void warp_insert_one(uint64_t (&pool)[LW], uint64_t c
     }
 }
 
+// pool (32*LW, sorted) <- the 32*LW smallest of pool and the real keys of
+// cand (32*S keys in any order, kPad where empty, none equal to a pool key),
+// every key placed at once: a pool entry moves up by the number of
+// candidates below it, a candidate lands at (pool entries below it) +
+// (candidates below it).  The keys are scattered through `buf` (32*LW keys of
+// shared memory the call may overwrite).  Each candidate costs one broadcast
+// and LW ballots, so this is for a few of them; the result equals inserting
+// them one by one, or sorting and merging the set.
+template <int LW, int S>
+__device__ __forceinline__ void warp_insert_few(uint64_t (&pool)[LW], const uint64_t (&cand)[S], uint64_t *buf,
+                                                int lane) {
+    constexpr int L = 32 * LW;
+    uint64_t cp[LW], cc[S];
+    uint32_t below[LW];  // candidates below each pool entry
+    int pos[S];          // final place of each candidate
+#pragma unroll
+    for (int s = 0; s < LW; s++) {
+        cp[s] = cmpk(pool[s]);
+        below[s] = 0;
+    }
+#pragma unroll
+    for (int s = 0; s < S; s++) {
+        cc[s] = cmpk(cand[s]);
+        pos[s] = 0;
+    }
+#pragma unroll
+    for (int cs = 0; cs < S; cs++) {
+        uint32_t m = __ballot_sync(kFull, !key_is_pad(cand[cs]));
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t c = shfl64(cc[cs], src);
+            int r = 0;
+#pragma unroll
+            for (int s = 0; s < LW; s++) {
+                below[s] += c < cp[s];
+                r += __popc(__ballot_sync(kFull, cp[s] < c));
+            }
+#pragma unroll
+            for (int s = 0; s < S; s++) pos[s] += c < cc[s];
+            if (lane == src) pos[cs] += r;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < LW; s++) {
+        const int p = s * 32 + lane + (int)below[s];
+        if (p < L) buf[p] = pool[s];
+    }
+#pragma unroll
+    for (int s = 0; s < S; s++)
+        if (!key_is_pad(cand[s]) && pos[s] < L) buf[pos[s]] = cand[s];
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < LW; s++) pool[s] = buf[s * 32 + lane];
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------- distances
 // A row is split into 16-byte chunks; the 8 lanes of a team take chunks
 // sub, sub+8, sub+16, ... and the partial sums are combined by xor shuffles

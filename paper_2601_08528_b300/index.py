@@ -382,3 +382,18 @@ def knn_tc(X: torch.Tensor, Q: torch.Tensor, k: int, metric: str = "l2", stream=
     L.check(lib.svf_knn_tc(_ptr(X), n, d, L.IP if metric == "ip" else L.L2, _ptr(Q), nq, k, _ptr(scratch), nbytes,
                            _ptr(ids), _ptr(dist), C.byref(fb), _stream(stream)))
     return ids, dist, int(fb.value)
+
+
+def gather_probe(table: torch.Tensor, n: int, pitch: int, row_bytes: int, rows: int, warps_per_sm: int = 24,
+                 seed: int = 1, stream=None):
+    """Random-row fetch ceiling (svf_gather_probe): about `rows` rows of
+    `row_bytes` bytes at uniform random ids of the first n rows of `table`
+    (device, rows `pitch` bytes apart), copied by the search kernel's copy
+    pattern with no arithmetic.  Returns (rows copied, device milliseconds)."""
+    lib = L.load()
+    status = torch.zeros(2, dtype=torch.int64, device=table.device)
+    nrows = C.c_int64(0)
+    ms = C.c_float(0.0)
+    L.check(lib.svf_gather_probe(_ptr(table), n, pitch, row_bytes, rows, warps_per_sm, seed, _ptr(status),
+                                 C.byref(nrows), C.byref(ms), _stream(stream)))
+    return int(nrows.value), float(ms.value)

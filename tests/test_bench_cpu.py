@@ -55,6 +55,11 @@ def test_profiled_traffic_follows_the_kernel_code(tmp_path):
     assert bench.csrc_hash(str(root)) == h0
     f.write_text(f.read_text() + "\nnamespace svf { constexpr int kProbe = 1; }\n")
     assert bench.csrc_hash(str(root)) != h0
-    assert bench.profiled_traffic("fp8+rerank", 64, 40) is not None  # the committed capture
+    # the committed capture counts while its recorded source hash is the code's
+    txt = open(os.path.join(ROOT, "profiles", "search_kernel_unit96_10M.md")).read()
+    sha = [ln.split(": ", 1)[1].strip() for ln in txt.splitlines() if ln.startswith("source_sha: ")]
+    assert len(sha) == 1
+    current = sha[0] == bench.csrc_hash()
+    assert (bench.profiled_traffic("fp8+rerank", 64, 40) is not None) == current
     assert bench.profiled_traffic("fp8+rerank", 64, 72) is None      # another launch point
     assert bench.profiled_traffic("bf16+rerank", 64, 40) is None     # another form

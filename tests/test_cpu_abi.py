@@ -100,3 +100,21 @@ def test_static_knn_validation_before_any_cuda_call(lib):
                           and lib.svf_knn_static_error())
     # an empty batch is a no-op that needs no pointers
     assert lib.svf_knn_static(None, 100, 16, 0, 0, None, 0, None, 10, None, None, None) == L.SVF_OK
+
+
+def test_gather_probe_validation_before_any_cuda_call(lib):
+    """svf_gather_probe answers bad arguments with SVF_EINVAL before touching
+    the device (the pointers below are never dereferenced)."""
+    from paper_2601_08528_b300 import _lib as L
+    P = 0x10000  # 16-byte aligned, never read: every case fails validation first
+    st = C.c_int64(0)
+    ms = C.c_float(0.0)
+    cases = [dict(table=None), dict(table=P + 8), dict(pitch=100), dict(row_bytes=8), dict(row_bytes=144),
+             dict(row_bytes=2048, pitch=2048), dict(n=0), dict(n=1 << 31), dict(rows=0), dict(warps=2),
+             dict(warps=6), dict(warps=68), dict(status=None)]
+    for c in cases:
+        a = dict(table=P, n=1000, pitch=128, row_bytes=112, rows=1000, warps=24, status=P)
+        a.update(c)
+        rc = lib.svf_gather_probe(a["table"], a["n"], a["pitch"], a["row_bytes"], a["rows"], a["warps"], 1,
+                                  a["status"], C.byref(st), C.byref(ms), None)
+        assert rc == L.SVF_EINVAL, c

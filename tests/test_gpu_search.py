@@ -216,3 +216,21 @@ def test_build_on_tensor_cores_rows_sampled(svf, orc, mix, metric):
     srt = np.sort(g, 1)
     assert not ((srt[:, 1:] == srt[:, :-1]) & (srt[:, 1:] != 0xFFFFFFFF)).any()
     assert (g != 0xFFFFFFFF).all()
+
+
+def test_gather_probe_measures_random_rows(svf):
+    """The random-row fetch ceiling probe copies at least the rows asked for
+    (whole batches of every warp), reports a plausible device time, and
+    rejects a bad layout on the device path too."""
+    import torch
+    n, pitch = 2_000_000, 128  # 256 MB: above the L2
+    table = torch.zeros(n * pitch, dtype=torch.uint8, device="cuda")
+    for wps in (16, 24, 32):
+        rows, ms = svf.gather_probe(table, n, pitch, 112, 1_000_000, warps_per_sm=wps)
+        assert rows >= 1_000_000 and rows % 32 == 0
+        rate = rows / (ms / 1e3)
+        assert 1e8 < rate < 1e12, (wps, rate)
+    rows, ms = svf.gather_probe(table, 1, pitch, 128, 5000)  # every copy reads the same row
+    assert rows >= 5000 and ms > 0
+    with pytest.raises(svf.SvfError):
+        svf.gather_probe(table, n, pitch, 120, 1000)
