@@ -631,6 +631,20 @@ __global__ void self_ids_kernel(const int32_t *idx, int64_t m, int64_t q0, int64
     if (i < m) out[i] = q0 + idx[i];
 }
 
+// Rows X[ids[i]] -> out[i] (fp32, d values each).
+__global__ void gather_ids_kernel(const float *X, int d, const int64_t *ids, int64_t m, float *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * d) return;
+    out[i] = X[ids[i / d] * d + i % d];
+}
+
+// keys[i] (k per row) -> out[ids[i]] (k per row).
+__global__ void scatter_ids_kernel(const uint64_t *keys, const int64_t *ids, int64_t m, int k, uint64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * k) return;
+    out[ids[i / k] * k + i % k] = keys[i];
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -839,7 +853,34 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
     const int splits = build_splits(K);
     const int wpb = 4;
     const size_t bsm = (size_t)wpb * KP * 4;
-    int64_t fallback = 0;
+    // Rows whose certificate failed wait in gself (absolute ids) until a
+    // chunk's worth has gathered; the exact SIMT scan then handles them in one
+    // launch (its grid is one block per 32 queries, so a few hundred rows per
+    // chunk would leave most SMs idle while every block reads the whole store).
+    float *gq = reinterpret_cast<float *>(scratch + L.gq);
+    uint64_t *gk = reinterpret_cast<uint64_t *>(scratch + L.gk);
+    int64_t *gself = reinterpret_cast<int64_t *>(scratch + L.gself);
+    int64_t fallback = 0, npend = 0;
+    auto flush = [&]() -> int {
+        if (npend == 0) return SVF_OK;
+        gather_ids_kernel<<<(unsigned)((npend * d + 255) / 256), 256, 0, st>>>(Xf, d, gself, npend, gq);
+        KnnArgs ka{};
+        ka.X = X;
+        ka.n = n;
+        ka.Q = gq;
+        ka.q_row_bytes = d * 4;
+        ka.nq = npend;
+        ka.self = gself;
+        ka.self_base = -1;
+        ka.k = K;
+        ka.out_keys = gk;
+        CUDA_TRY(launch_knn(ka, st));
+        scatter_ids_kernel<<<(unsigned)((npend * K + 255) / 256), 256, 0, st>>>(gk, gself, npend, K, keys);
+        CUDA_TRY(cudaGetLastError());
+        fallback += npend;
+        npend = 0;
+        return SVF_OK;
+    };
     for (int64_t q0 = 0; q0 < n; q0 += L.chunk) {
         const int64_t nq = std::min(L.chunk, n - q0);
         TcPass pass{};
@@ -866,27 +907,14 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
         if (hf[1]) return fail(SVF_ETIMEOUT, "build: a tensor-core pipeline wait gave up");
         const int64_t m = (int64_t)hf[0];
         if (m > 0) {
-            float *gq = reinterpret_cast<float *>(scratch + L.gq);
-            uint64_t *gk = reinterpret_cast<uint64_t *>(scratch + L.gk);
-            int64_t *gself = reinterpret_cast<int64_t *>(scratch + L.gself);
-            gather_rows_kernel<<<(unsigned)((m * d + 255) / 256), 256, 0, st>>>(Xf + q0 * d, d, flagged, m, gq);
-            self_ids_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(flagged, m, q0, gself);
-            KnnArgs ka{};
-            ka.X = X;
-            ka.n = n;
-            ka.Q = gq;
-            ka.q_row_bytes = d * 4;
-            ka.nq = m;
-            ka.self = gself;
-            ka.self_base = -1;
-            ka.k = K;
-            ka.out_keys = gk;
-            CUDA_TRY(launch_knn(ka, st));
-            scatter_keys_kernel<<<(unsigned)((m * K + 255) / 256), 256, 0, st>>>(gk, flagged, m, K, keys + q0 * K);
+            if (npend + m > L.chunk)
+                if (int rc = flush()) return rc;
+            self_ids_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(flagged, m, q0, gself + npend);
             CUDA_TRY(cudaGetLastError());
-            fallback += m;
+            npend += m;
         }
     }
+    if (int rc = flush()) return rc;
     if (out_fallback) *out_fallback = fallback;
     return SVF_OK;
 }
