@@ -163,6 +163,7 @@ typedef struct {
     uint64_t promoted;          /* tiered store: rows promoted into the cache */
     uint64_t evicted;           /* tiered store: cached rows evicted */
     uint64_t build_fallback;    /* last build: rows whose tensor-core neighbours were recomputed by the exact scan */
+    uint64_t build_tensor_core; /* last build: 1 if its exact 2R-NN came from the tensor-core scan, else 0 */
 } svf_counters;
 
 typedef struct svf_index svf_index;

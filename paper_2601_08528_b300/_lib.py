@@ -60,7 +60,7 @@ class Counters(C.Structure):
                 ("search_iters", C.c_uint64), ("search_evals", C.c_uint64), ("hash_resets", C.c_uint64),
                 ("repaired_rows", C.c_uint64), ("reverse_targets", C.c_uint64), ("cache_hits", C.c_uint64),
                 ("cache_misses", C.c_uint64), ("promoted", C.c_uint64), ("evicted", C.c_uint64),
-                ("build_fallback", C.c_uint64)]
+                ("build_fallback", C.c_uint64), ("build_tensor_core", C.c_uint64)]
 
 
 class TierParams(C.Structure):

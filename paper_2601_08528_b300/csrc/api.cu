@@ -190,9 +190,11 @@ int svf_build(svf_index *h, const void *X, int64_t n, void *stream) {
                               keys, &fb, st);
             if (rc) return rc;
             h->build_fallback = fb;
+            h->build_tc = true;
         } else {
             CUDA_TRY(launch_knn_self(P, n, 0, n, K, keys, st));
             h->build_fallback = 0;
+            h->build_tc = false;
         }
         PruneArgs a{};
         a.X = P;
@@ -476,6 +478,7 @@ int svf_stats(svf_index *h, svf_counters *out) {
     out->promoted = s[kStPromoted];
     out->evicted = s[kStEvicted];
     out->build_fallback = (uint64_t)h->build_fallback;
+    out->build_tensor_core = h->build_tc ? 1u : 0u;
     return SVF_OK;
 }
 

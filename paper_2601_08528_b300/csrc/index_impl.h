@@ -115,6 +115,7 @@ struct svf_index {
     int64_t n_used = 0;
     uint64_t repaired = 0;
     int64_t build_fallback = 0;  // rows of the last build whose tensor-core certificate failed
+    bool build_tc = false;       // the last build's 2R-NN came from the tensor-core scan
     cudaStream_t last = nullptr;
     svf::Tier tier;
     svf::Consol cons;

@@ -410,6 +410,25 @@ __global__ void to_bf16_kernel(const float *X, int64_t n, int d, int kp, __nv_bf
     if (lane == 0 && norms) norms[r] = ss;
 }
 
+// uint8 rows -> bf16 rows padded to kp columns (+ squared norms).  Every
+// value 0..255 is exact in bf16, and for d <= 128 every product and every sum
+// of them is an integer below 2^24, so the tensor-core pass computes the exact
+// distances in fp32.
+__global__ void u8_to_bf16_kernel(const uint8_t *X, int64_t n, int d, int kp, __nv_bfloat16 *out, float *norms) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) return;
+    uint32_t ss = 0;
+    for (int c = lane; c < kp; c += 32) {
+        const uint32_t v = c < d ? X[r * d + c] : 0u;
+        out[r * kp + c] = __float2bfloat16_rn((float)v);
+        ss += v * v;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) ss += __shfl_xor_sync(kFull, ss, m);
+    if (lane == 0 && norms) norms[r] = (float)ss;
+}
+
 __global__ void max_kernel(const float *v, int64_t n, unsigned int *out) {
     float m = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -534,24 +553,48 @@ __global__ void scatter_keys_kernel(const uint64_t *keys, const int32_t *idx, in
 // rescore_kernel (rows outside every list have approximate distance >= the
 // smallest list bound); a query that fails it, or has fewer than K
 // candidates, is flagged for the exact SIMT scan.
-template <int NPL>
-__global__ void band_rescore_kernel(const float *X, int d, int metric, const unsigned int *maxnorm2, int lists,
+//
+// U8 (a uint8 store): the approximate distances are exact (u8_to_bf16_kernel),
+// so eps_c is 0, the band is the candidates at or below a_K, the exact
+// distances are integers (the store's keys: squared L2, or -dot through the
+// order-preserving map) and the certificate is that the smallest list bound
+// exceeds D_K strictly (a row left out of every list with the same distance
+// could precede the K-th by id).
+template <int NPL, bool U8>
+__global__ void band_rescore_kernel(const void *Xv, int d, int metric, const unsigned int *maxnorm2, int lists,
                                     const float *cand_d, const uint32_t *cand_i, int64_t q0, int64_t nq, int K,
                                     float eps_c, uint64_t *out_keys, int32_t *flagged, unsigned long long *nflag) {
-    extern __shared__ float4 bq[];  // per warp: the query row (d <= 128 floats)
+    extern __shared__ float4 bq[];  // per warp: the query row (d <= 128 floats, or d bytes)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (q >= nq) return;
     const int nc = lists * KC;
     const uint32_t self = (uint32_t)(q0 + q);
-    const float *qr = X + (q0 + q) * d;
+    const float *X = reinterpret_cast<const float *>(Xv);
+    const uint8_t *X8 = reinterpret_cast<const uint8_t *>(Xv);
     float4 *qs = bq + wib * (KP / 4);
-    for (int c = lane; c < d / 4; c += 32) qs[c] = reinterpret_cast<const float4 *>(qr)[c];
-    __syncwarp();
     float qn = 0.f;
-    for (int c = lane; c < d; c += 32) qn = fmaf(qr[c], qr[c], qn);
+    if constexpr (U8) {
+        const uint4 *qr8 = reinterpret_cast<const uint4 *>(X8 + (q0 + q) * d);
+        uint4 *qs8 = reinterpret_cast<uint4 *>(qs);
+        for (int c = lane; c < d / 16; c += 32) qs8[c] = qr8[c];
+        __syncwarp();
+        uint32_t qi = 0;
+        for (int c = lane; c < d; c += 32) {
+            const uint32_t v = X8[(q0 + q) * d + c];
+            qi += v * v;
+        }
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) qn += __shfl_xor_sync(kFull, qn, m);
+        for (int m = 16; m > 0; m >>= 1) qi += __shfl_xor_sync(kFull, qi, m);
+        qn = (float)qi;
+    } else {
+        const float *qr = X + (q0 + q) * d;
+        for (int c = lane; c < d / 4; c += 32) qs[c] = reinterpret_cast<const float4 *>(qr)[c];
+        __syncwarp();
+        for (int c = lane; c < d; c += 32) qn = fmaf(qr[c], qr[c], qn);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) qn += __shfl_xor_sync(kFull, qn, m);
+    }
     float bound = INFINITY;
     for (int s = lane; s < lists; s += 32) bound = fminf(bound, cand_d[(q * lists + s) * KC + KC - 1]);
 #pragma unroll
@@ -582,7 +625,31 @@ __global__ void band_rescore_kernel(const float *X, int d, int metric, const uns
         for (int s = 0; s < NPL; s++) {
             const int e = s * 32 + lane;
             uint64_t kx = kPad;
-            if (e < nb) {
+            if (e < nb && U8) {
+                // the row in 16-byte loads, exact in int32
+                const uint32_t id = key_id(ak[s]);
+                const uint4 *xr = reinterpret_cast<const uint4 *>(X8 + (int64_t)id * d);
+                const uint4 *qs8 = reinterpret_cast<const uint4 *>(qs);
+                uint32_t acc = 0;
+#pragma unroll 8
+                for (int c = 0; c < d / 16; c++) {
+                    const uint4 x = __ldg(xr + c), qv = qs8[c];
+                    if (metric == SVF_IP) {
+                        acc = __dp4a(x.x, qv.x, acc);
+                        acc = __dp4a(x.y, qv.y, acc);
+                        acc = __dp4a(x.z, qv.z, acc);
+                        acc = __dp4a(x.w, qv.w, acc);
+                    } else {
+                        const uint32_t a0 = __vabsdiffu4(x.x, qv.x), a1 = __vabsdiffu4(x.y, qv.y),
+                                       a2 = __vabsdiffu4(x.z, qv.z), a3 = __vabsdiffu4(x.w, qv.w);
+                        acc = __dp4a(a0, a0, acc);
+                        acc = __dp4a(a1, a1, acc);
+                        acc = __dp4a(a2, a2, acc);
+                        acc = __dp4a(a3, a3, acc);
+                    }
+                }
+                kx = make_key(metric == SVF_IP ? ((uint32_t)(-(int32_t)acc) ^ 0x80000000u) : acc, id);
+            } else if (e < nb) {
                 // the row in 16-byte loads, summed in element order
                 const uint32_t id = key_id(ak[s]);
                 const float4 *xr = reinterpret_cast<const float4 *>(X + (int64_t)id * d);
@@ -611,7 +678,8 @@ __global__ void band_rescore_kernel(const float *X, int d, int metric, const uns
 #pragma unroll
         for (int s = 0; s < NPL; s++)
             if (s == ((K - 1) >> 5)) dK = shfl64(ak[s], (K - 1) & 31);
-        const float DK = fkey_inv((uint32_t)(dK >> 32));
+        const uint32_t dkk = (uint32_t)(dK >> 32);
+        const float DK = !U8 ? fkey_inv(dkk) : metric == SVF_IP ? (float)(int32_t)(dkk ^ 0x80000000u) : (float)dkk;
         const float b = metric == SVF_L2 ? bound + qn : bound;
         fail = key_is_pad(dK) || (!(b - eps > DK) && isfinite(bound));
     }
@@ -633,6 +701,13 @@ __global__ void self_ids_kernel(const int32_t *idx, int64_t m, int64_t q0, int64
 
 // Rows X[ids[i]] -> out[i] (fp32, d values each).
 __global__ void gather_ids_kernel(const float *X, int d, const int64_t *ids, int64_t m, float *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * d) return;
+    out[i] = X[ids[i / d] * d + i % d];
+}
+
+// uint8 rows X[ids[i]] -> out[i] (d bytes each).
+__global__ void gather_ids_u8_kernel(const uint8_t *X, int d, const int64_t *ids, int64_t m, uint8_t *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m * d) return;
     out[i] = X[ids[i / d] * d + i % d];
@@ -782,8 +857,10 @@ TcLayout tc_layout(int64_t n, int64_t nq, int k, int d) {
 // ---------------------------------------------------------------- build
 // Slices of the build's scan: 2 * splits lists of KC candidates hold four
 // times the K neighbours wanted, so each list's bound lies far beyond them.
-constexpr int kBuildNPL = 8;                    // candidates per lane in band_rescore_kernel (<= 256)
+constexpr int kBuildNPLMax = 16;  // candidates per lane in band_rescore_kernel: at most 512 per row
 int build_splits(int K) { return std::max(1, (4 * K + 2 * KC - 1) / (2 * KC)); }
+// candidates per lane for K: 8 (256 candidates, K <= 64) or 16 (512, K <= 128)
+int build_npl(int K) { return 2 * build_splits(K) * KC <= 32 * 8 ? 8 : 16; }
 
 struct TcBuildLayout {
     size_t xb, norms, maxn, cd, ci, seed, flagged, nflag, gq, gk, gself, total;
@@ -822,8 +899,11 @@ TcBuildLayout tc_build_layout(int64_t n, int d, int K) {
 // which for data far from the origin exceeds the gaps between neighbour
 // distances, so the certificate would fail for most rows.
 bool tc_build_applies(int dtype, int metric, int d, int64_t n, int K) {
-    return dtype == SVF_F32 && metric == SVF_IP && d % 16 == 0 && d <= KP && n >= kTcBuildMinRows && K >= 1 &&
-           2 * build_splits(K) * KC <= 32 * kBuildNPL && n < (1ll << 31);
+    // fp32: inner product only (the bf16 bound above); uint8: exact for both
+    // metrics (d <= 128: every partial sum an integer below 2^24)
+    const bool kind = (dtype == SVF_F32 && metric == SVF_IP) || (dtype == SVF_U8 && (metric == SVF_L2 || metric == SVF_IP));
+    return kind && d % 16 == 0 && d <= KP && n >= kTcBuildMinRows && K >= 1 &&
+           2 * build_splits(K) * KC <= 32 * kBuildNPLMax && n < (1ll << 31);
 }
 
 size_t tc_build_scratch_bytes(int64_t n, int d, int K) { return tc_build_layout(n, d, K).total; }
@@ -837,7 +917,9 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
     const int d = X.d, kp = (d + KA - 1) / KA * KA;
     const TcBuildLayout L = tc_build_layout(n, d, K);
     if (bytes < L.total) return fail(SVF_EINVAL, "build scratch of %zu bytes, need %zu", bytes, L.total);
+    const bool u8 = X.dtype == SVF_U8;
     const float *Xf = reinterpret_cast<const float *>(X.base);
+    const uint8_t *X8 = X.base;
     auto *xb = reinterpret_cast<__nv_bfloat16 *>(scratch + L.xb);
     float *norms = reinterpret_cast<float *>(scratch + L.norms);
     unsigned int *maxn = reinterpret_cast<unsigned int *>(scratch + L.maxn);
@@ -846,7 +928,10 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
     int32_t *flagged = reinterpret_cast<int32_t *>(scratch + L.flagged);
     unsigned long long *nflag = reinterpret_cast<unsigned long long *>(scratch + L.nflag);
     unsigned long long *status = nflag + 8;
-    to_bf16_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(Xf, n, d, kp, xb, norms);
+    if (u8)
+        u8_to_bf16_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(X8, n, d, kp, xb, norms);
+    else
+        to_bf16_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(Xf, n, d, kp, xb, norms);
     CUDA_TRY(cudaMemsetAsync(maxn, 0, 4, st));
     CUDA_TRY(cudaMemsetAsync(status, 0, 8, st));
     max_kernel<<<296, 256, 0, st>>>(norms, n, maxn);
@@ -863,12 +948,16 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
     int64_t fallback = 0, npend = 0;
     auto flush = [&]() -> int {
         if (npend == 0) return SVF_OK;
-        gather_ids_kernel<<<(unsigned)((npend * d + 255) / 256), 256, 0, st>>>(Xf, d, gself, npend, gq);
+        if (u8)
+            gather_ids_u8_kernel<<<(unsigned)((npend * d + 255) / 256), 256, 0, st>>>(
+                X8, d, gself, npend, reinterpret_cast<uint8_t *>(gq));
+        else
+            gather_ids_kernel<<<(unsigned)((npend * d + 255) / 256), 256, 0, st>>>(Xf, d, gself, npend, gq);
         KnnArgs ka{};
         ka.X = X;
         ka.n = n;
         ka.Q = gq;
-        ka.q_row_bytes = d * 4;
+        ka.q_row_bytes = u8 ? d : d * 4;
         ka.nq = npend;
         ka.self = gself;
         ka.self_base = -1;
@@ -897,8 +986,27 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
         pass.status = status;
         if (int rc = tc_pass(pass, splits, splits, st)) return rc;
         CUDA_TRY(cudaMemsetAsync(nflag, 0, 8, st));
-        band_rescore_kernel<kBuildNPL><<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, bsm, st>>>(
-            Xf, d, X.metric, maxn, 2 * splits, cd, ci, q0, nq, K, kBf16ErrC, keys + q0 * K, flagged, nflag);
+        {
+            const dim3 g((unsigned)((nq + wpb - 1) / wpb)), b(wpb * 32);
+            const float c = u8 ? 0.f : kBf16ErrC;  // uint8: the approximate distances are exact
+            const int lists = 2 * splits;
+            uint64_t *kq = keys + q0 * K;
+            if (build_npl(K) == 8) {
+                if (u8)
+                    band_rescore_kernel<8, true><<<g, b, bsm, st>>>(X8, d, X.metric, maxn, lists, cd, ci, q0, nq, K, c,
+                                                                     kq, flagged, nflag);
+                else
+                    band_rescore_kernel<8, false><<<g, b, bsm, st>>>(Xf, d, X.metric, maxn, lists, cd, ci, q0, nq, K, c,
+                                                                      kq, flagged, nflag);
+            } else {
+                if (u8)
+                    band_rescore_kernel<16, true><<<g, b, bsm, st>>>(X8, d, X.metric, maxn, lists, cd, ci, q0, nq, K, c,
+                                                                      kq, flagged, nflag);
+                else
+                    band_rescore_kernel<16, false><<<g, b, bsm, st>>>(Xf, d, X.metric, maxn, lists, cd, ci, q0, nq, K,
+                                                                       c, kq, flagged, nflag);
+            }
+        }
         CUDA_TRY(cudaGetLastError());
         unsigned long long hf[2] = {0, 0};
         CUDA_TRY(cudaMemcpyAsync(&hf[0], nflag, 8, cudaMemcpyDeviceToHost, st));

@@ -11,8 +11,9 @@ FP64 oracle run on the same inputs.
   a near tie counted and bounded, and recall@10 against exact kNN equal to
   the oracle's within 0.2 points (exact kNN by the oracle's FP64 brute force
   on 500 sampled queries, and by the tensor-core scan on all 10,000).
-* u8, 1M x 128 uint8 squared L2, R = 64: the GPU's exact build checked row by
-  row on 2,000 sampled vertices (exact 128-NN + prune by the oracle); all
+* u8, 1M x 128 uint8 squared L2, R = 64: the GPU's exact build (the exact
+  tensor-core scan of uint8 rows) checked row by row on 2,000 sampled
+  vertices (exact 128-NN + prune by the oracle); all
   10,000 queries bit-exact at L = 64 and L = 128; the 10 % insert stream (ten
   batches of 10,000) compared over the whole graph with the oracle's inserts
   after every batch, and all queries again on the grown graph; a global
@@ -158,6 +159,7 @@ def u8(svf):
 
 def test_u8_1M_build_rows_sampled(orc, u8):
     X, ix, g, Q = u8
+    assert ix.stats()["build_tensor_core"] == 1  # the exact 128-NN came from the tensor-core scan
     graph_invariants(g, N8)
     vs = sample(N8, 2000, 21)
     st = orc.Store.from_vectors(X[:N8], "l2")

@@ -201,6 +201,7 @@ def test_build_on_tensor_cores_rows_sampled(svf, orc, mix, metric):
     g = P.as_u32(ix.graph[:n].cpu().numpy())
     s = ix.stats()
     assert s["build_fallback"] < (n // 10 if metric == "ip" else 1)
+    assert s["build_tensor_core"] == (1 if metric == "ip" else 0)
     vs = np.sort(np.random.default_rng(282).choice(n, 400, replace=False))
     st = orc.Store.from_vectors(X, metric)
     ids, d, kgap = orc.knn(st, X[vs], 2 * R, self_ids=vs.astype(np.int64))
@@ -216,6 +217,30 @@ def test_build_on_tensor_cores_rows_sampled(svf, orc, mix, metric):
     srt = np.sort(g, 1)
     assert not ((srt[:, 1:] == srt[:, :-1]) & (srt[:, 1:] != 0xFFFFFFFF)).any()
     assert (g != 0xFFFFFFFF).all()
+
+
+@pytest.mark.parametrize("R,metric", [(64, "l2"), (32, "l2"), (64, "ip")])
+def test_build_u8_on_tensor_cores_bit_exact(svf, orc, R, metric):
+    """uint8 stores of n >= 65,536 rows take the tensor-core scan too: values
+    0..255 are exact in bf16 and every partial sum of products is an integer
+    below 2^24, so the scan's distances are exact, the certificate needs no
+    error band, and sampled graph rows equal the oracle's exact 2R-NN + RNG
+    prune bit for bit (K = 128 runs the 512-candidate re-score)."""
+    n = 70_000
+    X = synth.sample("u8", n, 283)
+    ix = svf.Index(X.shape[1], n, dtype="u8", metric=metric, R=R, max_batch=n)
+    ix.build(torch.from_numpy(X).cuda())
+    s = ix.stats()
+    assert s["build_tensor_core"] == 1
+    assert s["build_fallback"] < n // 10
+    g = P.as_u32(ix.graph[:n].cpu().numpy())
+    vs = np.sort(np.random.default_rng(284).choice(n, 300, replace=False))
+    st = orc.Store.from_vectors(X, metric)
+    ids, d, _ = orc.knn(st, X[vs], 2 * R, self_ids=vs.astype(np.int64))
+    for i, v in enumerate(vs):
+        row, _ = orc.prune(st, ids[i], d[i], R)
+        np.testing.assert_array_equal(g[v], row, err_msg=f"row {v}")
+    assert not (g == np.arange(n)[:, None]).any()
 
 
 def test_gather_probe_measures_random_rows(svf):
