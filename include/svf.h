@@ -186,11 +186,15 @@ int svf_attach(svf_index *h, int64_t n_used);
  * of d primary elements (n <= n_cap, n <= max_batch).  Copies X into the
  * store, computes the exact 2R nearest neighbours of every row (self
  * excluded) and prunes each list to R (Sec. 5.1 reordering).  Resets
- * deletions; n_used = n.  For an fp32 inner-product store with d <= 128,
- * 2R <= 64 and n >= 65,536 the neighbours come from the tensor cores (bf16 tcgen05 scan of
- * the rows against themselves, exact fp32 re-scoring of a certified band of
- * candidates, the exact scan for rows whose certificate fails); otherwise
- * from the exact SIMT scan.  Both give the exact 2R-NN by fp32 (distance, id). */
+ * deletions; n_used = n.  With d <= 128 (a multiple of 16), 2R <= 128 and
+ * n >= 65,536 the neighbours of an fp32 inner-product store or of a uint8
+ * store (either metric) come from the tensor cores: a bf16 tcgen05 scan of the
+ * rows against themselves, exact re-scoring of a certified band of candidates
+ * (fp32; for uint8 the scan is itself exact and the re-scoring is integer),
+ * and the exact scan for rows whose certificate fails; otherwise from the
+ * exact SIMT scan.  Every path gives the exact 2R-NN by (distance, id), the
+ * distance in fp32 for fp32 stores and in int32 for uint8 stores.  The
+ * counters' build_tensor_core tells which path the last build took. */
 int svf_build(svf_index *h, const void *X, int64_t n, void *stream);
 
 /* Search (Alg. 1): Q is device, nq rows of d elements (uint8 for a U8

@@ -37,8 +37,8 @@ inline void set_team(RowDesc &r) {
 }
 
 // Exact 2R-NN of the build on the tensor cores (tc_knn.cu): used for fp32
-// inner-product stores with d <= 128 and at least 2^16 rows; scratch inside
-// the workspace.
+// inner-product stores and uint8 stores with d <= 128, 2R <= 128 and at least
+// 2^16 rows; scratch inside the workspace.
 bool tc_build_applies(int dtype, int metric, int d, int64_t n, int K);
 size_t tc_build_scratch_bytes(int64_t n, int d, int K);
 int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t bytes, uint64_t *keys,

@@ -27,6 +27,13 @@
 //    if min_list(16th) - eps exceeds the k-th exact distance no row can be
 //    missing.  Queries that fail it are recomputed by the SIMT kernel
 //    (knn.cu).
+// 4. The build (tc_build_knn): the rows are their own queries, in chunks of
+//    131,072; band_rescore_kernel re-scores only the candidates within the
+//    error band of the 2R-th and certifies them the same way; the rows that
+//    fail are gathered across chunks and rescanned by the SIMT kernel.  For
+//    uint8 stores the bf16 copies are exact and every partial sum of the
+//    products is an integer below 2^24, so the scan's distances are exact,
+//    the band has no error margin and the re-scoring is in int32.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
