@@ -561,6 +561,9 @@ __global__ void scatter_keys_kernel(const uint64_t *keys, const int32_t *idx, in
 // smallest list bound); a query that fails it, or has fewer than K
 // candidates, is flagged for the exact SIMT scan.
 //
+// Query q is row q0 + q of the store, or row qids[q] when qids is set (the
+// second pass over the rows whose certificate failed).
+//
 // U8 (a uint8 store): the approximate distances are exact (u8_to_bf16_kernel),
 // so eps_c is 0, the band is the candidates at or below a_K, the exact
 // distances are integers (the store's keys: squared L2, or -dot through the
@@ -570,32 +573,34 @@ __global__ void scatter_keys_kernel(const uint64_t *keys, const int32_t *idx, in
 template <int NPL, bool U8>
 __global__ void band_rescore_kernel(const void *Xv, int d, int metric, const unsigned int *maxnorm2, int lists,
                                     const float *cand_d, const uint32_t *cand_i, int64_t q0, int64_t nq, int K,
-                                    float eps_c, uint64_t *out_keys, int32_t *flagged, unsigned long long *nflag) {
+                                    float eps_c, uint64_t *out_keys, int32_t *flagged, unsigned long long *nflag,
+                                    const int64_t *qids) {
     extern __shared__ float4 bq[];  // per warp: the query row (d <= 128 floats, or d bytes)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (q >= nq) return;
     const int nc = lists * KC;
-    const uint32_t self = (uint32_t)(q0 + q);
+    const int64_t qrow = qids ? qids[q] : q0 + q;  // the query's own row of the store
+    const uint32_t self = (uint32_t)qrow;
     const float *X = reinterpret_cast<const float *>(Xv);
     const uint8_t *X8 = reinterpret_cast<const uint8_t *>(Xv);
     float4 *qs = bq + wib * (KP / 4);
     float qn = 0.f;
     if constexpr (U8) {
-        const uint4 *qr8 = reinterpret_cast<const uint4 *>(X8 + (q0 + q) * d);
+        const uint4 *qr8 = reinterpret_cast<const uint4 *>(X8 + qrow * d);
         uint4 *qs8 = reinterpret_cast<uint4 *>(qs);
         for (int c = lane; c < d / 16; c += 32) qs8[c] = qr8[c];
         __syncwarp();
         uint32_t qi = 0;
         for (int c = lane; c < d; c += 32) {
-            const uint32_t v = X8[(q0 + q) * d + c];
+            const uint32_t v = X8[qrow * d + c];
             qi += v * v;
         }
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) qi += __shfl_xor_sync(kFull, qi, m);
         qn = (float)qi;
     } else {
-        const float *qr = X + (q0 + q) * d;
+        const float *qr = X + qrow * d;
         for (int c = lane; c < d / 4; c += 32) qs[c] = reinterpret_cast<const float4 *>(qr)[c];
         __syncwarp();
         for (int c = lane; c < d; c += 32) qn = fmaf(qr[c], qr[c], qn);
@@ -711,6 +716,19 @@ __global__ void gather_ids_kernel(const float *X, int d, const int64_t *ids, int
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m * d) return;
     out[i] = X[ids[i / d] * d + i % d];
+}
+
+// out[i] = ids[idx[i]]: store ids of the flagged entries of an id list.
+__global__ void pick_ids_kernel(const int32_t *idx, int64_t m, const int64_t *ids, int64_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = ids[idx[i]];
+}
+
+// bf16 rows xb[ids[i]] -> out[i] (kp values each).
+__global__ void gather_bf16_kernel(const __nv_bfloat16 *xb, int kp, const int64_t *ids, int64_t m, __nv_bfloat16 *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * kp) return;
+    out[i] = xb[ids[i / kp] * kp + i % kp];
 }
 
 // uint8 rows X[ids[i]] -> out[i] (d bytes each).
@@ -866,11 +884,9 @@ TcLayout tc_layout(int64_t n, int64_t nq, int k, int d) {
 // times the K neighbours wanted, so each list's bound lies far beyond them.
 constexpr int kBuildNPLMax = 16;  // candidates per lane in band_rescore_kernel: at most 512 per row
 int build_splits(int K) { return std::max(1, (4 * K + 2 * KC - 1) / (2 * KC)); }
-// candidates per lane for K: 8 (256 candidates, K <= 64) or 16 (512, K <= 128)
-int build_npl(int K) { return 2 * build_splits(K) * KC <= 32 * 8 ? 8 : 16; }
 
 struct TcBuildLayout {
-    size_t xb, norms, maxn, cd, ci, seed, flagged, nflag, gq, gk, gself, total;
+    size_t xb, norms, maxn, cd, ci, seed, flagged, nflag, gq, gk, gself, gfail, total;
     int64_t chunk;
 };
 
@@ -896,6 +912,7 @@ TcBuildLayout tc_build_layout(int64_t n, int d, int K) {
     L.gq = take((size_t)L.chunk * d * 4);
     L.gk = take((size_t)L.chunk * K * 8);
     L.gself = take((size_t)L.chunk * 8);
+    L.gfail = take((size_t)L.chunk * 8);
     L.total = o;
     return L;
 }
@@ -953,6 +970,29 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
     uint64_t *gk = reinterpret_cast<uint64_t *>(scratch + L.gk);
     int64_t *gself = reinterpret_cast<int64_t *>(scratch + L.gself);
     int64_t fallback = 0, npend = 0;
+    // band re-scoring of nq queries (rows q0.., or rows qids[..]) from `lists`
+    // candidate lists into kq[nq][K]; failing queries (local indices) land in
+    // flagged / nflag
+    const float eps_c = u8 ? 0.f : kBf16ErrC;  // uint8: the approximate distances are exact
+    auto band = [&](int lists, int64_t q0, int64_t nq, uint64_t *kq, const int64_t *qids) {
+        const dim3 g((unsigned)((nq + wpb - 1) / wpb)), b(wpb * 32);
+        if (lists * KC <= 32 * 8) {
+            if (u8)
+                band_rescore_kernel<8, true><<<g, b, bsm, st>>>(X8, d, X.metric, maxn, lists, cd, ci, q0, nq, K, eps_c,
+                                                                 kq, flagged, nflag, qids);
+            else
+                band_rescore_kernel<8, false><<<g, b, bsm, st>>>(Xf, d, X.metric, maxn, lists, cd, ci, q0, nq, K, eps_c,
+                                                                  kq, flagged, nflag, qids);
+        } else {
+            if (u8)
+                band_rescore_kernel<16, true><<<g, b, bsm, st>>>(X8, d, X.metric, maxn, lists, cd, ci, q0, nq, K, eps_c,
+                                                                  kq, flagged, nflag, qids);
+            else
+                band_rescore_kernel<16, false><<<g, b, bsm, st>>>(Xf, d, X.metric, maxn, lists, cd, ci, q0, nq, K,
+                                                                   eps_c, kq, flagged, nflag, qids);
+        }
+        return cudaGetLastError();
+    };
     auto flush = [&]() -> int {
         if (npend == 0) return SVF_OK;
         if (u8)
@@ -977,6 +1017,57 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
         npend = 0;
         return SVF_OK;
     };
+    // The pending rows first get a second pass of the same scan with twice
+    // the slices (each list covers half the rows, so its 16th entry -- the
+    // certificate's bound -- lies further out and the band has more
+    // candidates), in batches that fit the candidate buffers; the rows it
+    // certifies skip the SIMT scan.  Skipped when twice the lists exceed the
+    // re-score's 512 candidates (2R = 128).
+    const int splits2 = 2 * splits, lists2 = 2 * splits2;
+    auto resolve = [&]() -> int {
+        if (npend > 0 && lists2 * KC <= 32 * kBuildNPLMax) {
+            int64_t *gfail = reinterpret_cast<int64_t *>(scratch + L.gfail);
+            auto *qb2 = reinterpret_cast<__nv_bfloat16 *>(gq);  // m x kp bf16 fits the fp32 query rows' space
+            const int64_t B2 = L.chunk / 2;
+            int64_t nfail = 0;
+            for (int64_t p0 = 0; p0 < npend; p0 += B2) {
+                const int64_t m = std::min(B2, npend - p0);
+                gather_bf16_kernel<<<(unsigned)((m * kp + 255) / 256), 256, 0, st>>>(xb, kp, gself + p0, m, qb2);
+                TcPass p2{};
+                p2.xb = xb;
+                p2.qb = qb2;
+                p2.n = n;
+                p2.nq = m;
+                p2.kp = kp;
+                p2.metric = X.metric;
+                p2.norms = norms;
+                p2.cd = cd;
+                p2.ci = ci;
+                p2.seed = reinterpret_cast<float *>(scratch + L.seed);
+                p2.status = status;
+                if (int rc = tc_pass(p2, splits2, splits2, st)) return rc;
+                CUDA_TRY(cudaMemsetAsync(nflag, 0, 8, st));
+                CUDA_TRY(band(lists2, 0, m, gk, gself + p0));
+                // every row's keys to its place (a failed row's pads are overwritten by the SIMT scan)
+                scatter_ids_kernel<<<(unsigned)((m * K + 255) / 256), 256, 0, st>>>(gk, gself + p0, m, K, keys);
+                CUDA_TRY(cudaGetLastError());
+                unsigned long long hf[2] = {0, 0};
+                CUDA_TRY(cudaMemcpyAsync(&hf[0], nflag, 8, cudaMemcpyDeviceToHost, st));
+                CUDA_TRY(cudaMemcpyAsync(&hf[1], status, 8, cudaMemcpyDeviceToHost, st));
+                CUDA_TRY(cudaStreamSynchronize(st));
+                if (hf[1]) return fail(SVF_ETIMEOUT, "build: a tensor-core pipeline wait gave up");
+                const int64_t mf = (int64_t)hf[0];
+                if (mf > 0) {
+                    pick_ids_kernel<<<(unsigned)((mf + 255) / 256), 256, 0, st>>>(flagged, mf, gself + p0, gfail + nfail);
+                    CUDA_TRY(cudaGetLastError());
+                }
+                nfail += mf;
+            }
+            if (nfail > 0) CUDA_TRY(cudaMemcpyAsync(gself, gfail, (size_t)nfail * 8, cudaMemcpyDeviceToDevice, st));
+            npend = nfail;
+        }
+        return flush();
+    };
     for (int64_t q0 = 0; q0 < n; q0 += L.chunk) {
         const int64_t nq = std::min(L.chunk, n - q0);
         TcPass pass{};
@@ -993,28 +1084,7 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
         pass.status = status;
         if (int rc = tc_pass(pass, splits, splits, st)) return rc;
         CUDA_TRY(cudaMemsetAsync(nflag, 0, 8, st));
-        {
-            const dim3 g((unsigned)((nq + wpb - 1) / wpb)), b(wpb * 32);
-            const float c = u8 ? 0.f : kBf16ErrC;  // uint8: the approximate distances are exact
-            const int lists = 2 * splits;
-            uint64_t *kq = keys + q0 * K;
-            if (build_npl(K) == 8) {
-                if (u8)
-                    band_rescore_kernel<8, true><<<g, b, bsm, st>>>(X8, d, X.metric, maxn, lists, cd, ci, q0, nq, K, c,
-                                                                     kq, flagged, nflag);
-                else
-                    band_rescore_kernel<8, false><<<g, b, bsm, st>>>(Xf, d, X.metric, maxn, lists, cd, ci, q0, nq, K, c,
-                                                                      kq, flagged, nflag);
-            } else {
-                if (u8)
-                    band_rescore_kernel<16, true><<<g, b, bsm, st>>>(X8, d, X.metric, maxn, lists, cd, ci, q0, nq, K, c,
-                                                                      kq, flagged, nflag);
-                else
-                    band_rescore_kernel<16, false><<<g, b, bsm, st>>>(Xf, d, X.metric, maxn, lists, cd, ci, q0, nq, K,
-                                                                       c, kq, flagged, nflag);
-            }
-        }
-        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(band(2 * splits, q0, nq, keys + q0 * K, nullptr));
         unsigned long long hf[2] = {0, 0};
         CUDA_TRY(cudaMemcpyAsync(&hf[0], nflag, 8, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaMemcpyAsync(&hf[1], status, 8, cudaMemcpyDeviceToHost, st));
@@ -1023,13 +1093,13 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
         const int64_t m = (int64_t)hf[0];
         if (m > 0) {
             if (npend + m > L.chunk)
-                if (int rc = flush()) return rc;
+                if (int rc = resolve()) return rc;
             self_ids_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(flagged, m, q0, gself + npend);
             CUDA_TRY(cudaGetLastError());
             npend += m;
         }
     }
-    if (int rc = flush()) return rc;
+    if (int rc = resolve()) return rc;
     if (out_fallback) *out_fallback = fallback;
     return SVF_OK;
 }
