@@ -3,11 +3,12 @@
 // exhaustive scan (Sec. 6.1).  SIMT: fp32 FMA, or exact int32 for uint8
 // (|a-b| per byte with __vabsdiffu4, squares summed by __dp4a).
 //
-// A CTA owns 32 queries and streams the database in tiles of 64 rows; each
+// A CTA owns 32 queries and streams the database (or one slice of it) in tiles of 64 rows; each
 // thread accumulates a 2 x 4 block of distances from transposed shared-memory
 // tiles (32 words of the row per step).  Candidates below a query's current
 // k-th key are appended to a per-query buffer; after each tile one warp per
 // query sorts the buffer and merges it into the query's 128-entry list.
+#include <algorithm>
 #include <cstdint>
 
 #include "svf_internal.h"
@@ -19,8 +20,10 @@ constexpr int QB = 32, NB = 64, WC = 32;  // queries, rows, 32-bit words per ste
 constexpr int KMAX = 128;
 constexpr int THREADS = 256;
 
+// Rows [blockIdx.y * slice, ...) of the store when slice > 0 (out: [nq][gridDim.y][k]), else all rows
+// (out: [nq][k]).
 template <int DT>
-__global__ void __launch_bounds__(THREADS) knn_kernel(const KnnArgs a) {
+__global__ void __launch_bounds__(THREADS) knn_kernel(const KnnArgs a, int64_t slice, uint64_t *out) {
     extern __shared__ __align__(16) uint8_t sm[];
     uint64_t(*lists)[KMAX] = reinterpret_cast<uint64_t(*)[KMAX]>(sm);
     uint64_t(*buf)[NB] = reinterpret_cast<uint64_t(*)[NB]>(sm + sizeof(uint64_t) * QB * KMAX);
@@ -48,7 +51,9 @@ __global__ void __launch_bounds__(THREADS) knn_kernel(const KnnArgs a) {
     }
     __syncthreads();
 
-    for (int64_t r0 = 0; r0 < a.n; r0 += NB) {
+    const int64_t r_begin = slice > 0 ? (int64_t)blockIdx.y * slice : 0;
+    const int64_t r_end = slice > 0 ? (r_begin + slice < a.n ? r_begin + slice : a.n) : a.n;
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += NB) {
         float facc[2][4];
         uint32_t iacc[2][4];
 #pragma unroll
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(THREADS) knn_kernel(const KnnArgs a) {
             for (int i = tid; i < NB * WC; i += THREADS) {
                 int r = i / WC, w = i % WC;
                 int64_t gr = r0 + r;
-                Xs[w][r] = (gr < a.n && w0 + w < words)
+                Xs[w][r] = (gr < r_end && w0 + w < words)
                                ? __ldg(reinterpret_cast<const uint32_t *>(a.X.base + gr * a.X.pitch) + w0 + w)
                                : 0u;
             }
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(THREADS) knn_kernel(const KnnArgs a) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 int64_t gr = r0 + tn + 16 * j;
-                if (gr >= a.n || gr == selfq[i]) continue;
+                if (gr >= r_end || gr == selfq[i]) continue;
                 if (a.del && is_deleted(a.del, (uint32_t)gr)) continue;
                 uint32_t dk;
                 if constexpr (DT == SVF_U8)
@@ -147,7 +152,26 @@ __global__ void __launch_bounds__(THREADS) knn_kernel(const KnnArgs a) {
     }
     for (int i = tid; i < QB * a.k; i += THREADS) {
         int ql = i / a.k, j = i % a.k;
-        if (q0 + ql < a.nq) a.out_keys[(q0 + ql) * a.k + j] = lists[ql][j];
+        if (q0 + ql < a.nq) out[((q0 + ql) * gridDim.y + blockIdx.y) * a.k + j] = lists[ql][j];
+    }
+}
+
+// Warp per query: the best k of its s sorted slice lists (s * k <= 512 keys).
+__global__ void merge_slices_kernel(const uint64_t *part, int64_t nq, int s, int k, uint64_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    uint64_t v[16];
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+        const int e = t * 32 + lane;
+        v[t] = e < s * k ? part[q * s * k + e] : kPad;
+    }
+    warp_sort<16>(v, lane);
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int e = t * 32 + lane;
+        if (e < k) out[q * k + e] = v[t];
     }
 }
 
@@ -166,16 +190,30 @@ __global__ void keys_to_out_kernel(const uint64_t *keys, int64_t nq, int kin, in
 
 cudaError_t launch_knn(const KnnArgs &a, cudaStream_t st) {
     if (a.k < 1 || a.k > KMAX || a.nq <= 0) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((a.nq + QB - 1) / QB));
+    const int64_t qtiles = (a.nq + QB - 1) / QB;
     const size_t smem = sizeof(uint64_t) * QB * (KMAX + NB + 1) + sizeof(uint32_t) * WC * (QB + 1) +
                         sizeof(uint32_t) * WC * (NB + 1) + sizeof(int) * QB;
+    // slices: enough blocks for about three per SM, each slice list k keys,
+    // all of a query's slice lists together at most 512 keys, within the scratch
+    int s = 1;
+    if (a.part_keys) {
+        const int64_t want = ((int64_t)3 * sm_count() + qtiles - 1) / qtiles;
+        const int64_t fit = (int64_t)(a.part_bytes / ((size_t)a.nq * a.k * sizeof(uint64_t)));
+        s = (int)std::min<int64_t>(std::min<int64_t>(want, 512 / a.k), std::min<int64_t>(fit, 16));
+        if (s < 2) s = 1;
+    }
+    const int64_t slice = s > 1 ? ((a.n + s - 1) / s + NB - 1) / NB * NB : 0;
+    dim3 grid((unsigned)qtiles, (unsigned)s);
+    uint64_t *out = s > 1 ? a.part_keys : a.out_keys;
     if (a.X.dtype == SVF_U8) {
         cudaFuncSetAttribute(knn_kernel<SVF_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        knn_kernel<SVF_U8><<<grid, THREADS, smem, st>>>(a);
+        knn_kernel<SVF_U8><<<grid, THREADS, smem, st>>>(a, slice, out);
     } else {
         cudaFuncSetAttribute(knn_kernel<SVF_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        knn_kernel<SVF_F32><<<grid, THREADS, smem, st>>>(a);
+        knn_kernel<SVF_F32><<<grid, THREADS, smem, st>>>(a, slice, out);
     }
+    if (s > 1) merge_slices_kernel<<<(unsigned)((a.nq * 32 + 255) / 256), 256, 0, st>>>(a.part_keys, a.nq, s, a.k,
+                                                                                         a.out_keys);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,12 @@ struct KnnArgs {
     const uint32_t *del;   // skip deleted (device) or null
     int k;                 // <= 128
     uint64_t *out_keys;    // [nq][k] sorted keys (PAD-filled)
+    // Optional scratch for small batches: with it, the rows are split into
+    // slices scanned by separate blocks (one block per 32 queries would leave
+    // most SMs idle), each slice's exact top k lands here and a merge keeps
+    // the best k of each query.  Null: one block per 32 queries scans every row.
+    uint64_t *part_keys;
+    size_t part_bytes;
 };
 cudaError_t launch_knn(const KnnArgs &a, cudaStream_t st);
 // Same, with queries taken from the store itself (rows q0 .. q0+nq-1),

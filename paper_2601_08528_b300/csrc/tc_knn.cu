@@ -1010,6 +1010,9 @@ int tc_build_knn(const RowDesc &X, int64_t n, int K, uint8_t *scratch, size_t by
         ka.self_base = -1;
         ka.k = K;
         ka.out_keys = gk;
+        // the candidate lists are free here: a small batch is scanned in slices
+        ka.part_keys = reinterpret_cast<uint64_t *>(cd);
+        ka.part_bytes = (size_t)L.chunk * (2 * splits) * KC * sizeof(float);
         CUDA_TRY(launch_knn(ka, st));
         scatter_ids_kernel<<<(unsigned)((npend * K + 255) / 256), 256, 0, st>>>(gk, gself, npend, K, keys);
         CUDA_TRY(cudaGetLastError());

@@ -243,6 +243,32 @@ def test_build_u8_on_tensor_cores_bit_exact(svf, orc, R, metric):
     assert not (g == np.arange(n)[:, None]).any()
 
 
+@pytest.mark.parametrize("R", [32, 64])
+def test_build_rows_past_both_certificates_bit_exact(svf, orc, R):
+    """Rows whose neighbourhoods are exact ties (100 copies of each of 20
+    uint8 vectors: every list's bound equals the 2R-th distance, 0) fail the
+    certificate of the first scan and of the second (R = 32; R = 64 has
+    none), so the exact SIMT scan recomputes them, their batch split into
+    row slices whose lists are merged.  Those rows and sampled others equal
+    the oracle's exact 2R-NN + prune bit for bit."""
+    n = 70_000
+    X = synth.sample("u8", n, 285)
+    X[:2000] = np.repeat(X[:20], 100, axis=0)
+    ix = svf.Index(X.shape[1], n, dtype="u8", metric="l2", R=R, max_batch=n)
+    ix.build(torch.from_numpy(X).cuda())
+    s = ix.stats()
+    assert s["build_tensor_core"] == 1
+    assert s["build_fallback"] >= 2000
+    g = P.as_u32(ix.graph[:n].cpu().numpy())
+    rng = np.random.default_rng(286)
+    vs = np.sort(np.concatenate([rng.choice(2000, 120, replace=False), 2000 + rng.choice(n - 2000, 80, replace=False)]))
+    st = orc.Store.from_vectors(X, "l2")
+    ids, d, _ = orc.knn(st, X[vs], 2 * R, self_ids=vs.astype(np.int64))
+    for i, v in enumerate(vs):
+        row, _ = orc.prune(st, ids[i], d[i], R)
+        np.testing.assert_array_equal(g[v], row, err_msg=f"row {v}")
+
+
 def test_gather_probe_measures_random_rows(svf):
     """The random-row fetch ceiling probe copies at least the rows asked for
     (whole batches of every warp), reports a plausible device time, and
